@@ -1,0 +1,325 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with a copy of itself: hand-derived layered examples,
+the brute-force definition of the check-node rule, exact max-log / MAP marginals on a
+cycle-free code, noiseless decoding, brute-force ML decoding of a tiny code, IEEE binary16
+rounding against numpy's conversion, and cross-mode identities (int8 vs fp32).
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import SHAPES, encode_structured, generate_base_graph, info_bits, make_workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- hand-derived examples
+
+def _load(name):
+    return json.load(open(os.path.join(GOLDEN, name)))
+
+
+def test_hand_example_int8_z2():
+    g = _load("hand_layered_z2.json")
+    code, ex = g["code"], g["int8_offset1"]
+    base = np.array(code["base"], np.int16)
+    llr = np.array([ex["llr"]], np.int8)
+    for T in (1, 2):
+        r = oracle.decode_layered(base, code["K_b"], code["Z"], code["n_rows"], llr,
+                                  algo=oracle.OFFSET, offset_q=1, max_iter=T, early_stop=False,
+                                  punct=code["punct"], want_post=True, want_c2v=True)
+        assert r.post[0].tolist() == ex[f"T{T}"]["post"]
+        assert r.c2v[0].tolist() == ex[f"T{T}"]["c2v"]
+        assert r.iters[0] == T
+    r = oracle.decode_layered(base, code["K_b"], code["Z"], code["n_rows"], llr,
+                              algo=oracle.OFFSET, offset_q=1, max_iter=2, early_stop=True,
+                              punct=0)
+    assert r.iters[0] == ex["T2_early_stop_iters"]
+    assert r.bits[0].tolist() == ex["hard_bits_K"]
+
+
+def test_hand_example_fp32_z2():
+    g = _load("hand_layered_z2.json")
+    code, ex = g["code"], g["fp32_normalised_0.75"]
+    base = np.array(code["base"], np.int16)
+    llr = np.array([ex["llr"]], np.float32)
+    r = oracle.decode_layered(base, code["K_b"], code["Z"], code["n_rows"], llr,
+                              algo=oracle.NORMALISED, alpha=0.75, max_iter=1, early_stop=False,
+                              punct=0, want_post=True, want_c2v=True)
+    assert r.post[0].tolist() == ex["T1"]["post"]
+    assert r.c2v[0].tolist() == ex["T1"]["c2v"]
+
+
+def test_hand_example_saturation():
+    g = _load("hand_saturation_z1.json")
+    code, ex = g["code"], g["int8_offset1"]
+    base = np.array(code["base"], np.int16)
+    llr = np.array([ex["llr"]], np.int8)
+    for T in (1, 2):
+        r = oracle.decode_layered(base, code["K_b"], 1, code["n_rows"], llr, algo=oracle.OFFSET,
+                                  offset_q=1, max_iter=T, early_stop=False, punct=0,
+                                  want_post=True, want_c2v=True)
+        assert r.post[0].tolist() == ex[f"T{T}"]["post"]
+        assert r.c2v[0].tolist() == ex[f"T{T}"]["c2v"]
+    r = oracle.decode_layered(base, code["K_b"], 1, code["n_rows"], llr, algo=oracle.OFFSET,
+                              offset_q=1, max_iter=10, early_stop=True, punct=0)
+    assert r.iters[0] == ex["early_stop_iters"]
+    assert r.bits[0].tolist() == ex["hard_bits_K"]
+
+
+# ------------------------------------------------------------- P3: check-node closed form
+
+def _cn_brute(v, corr):
+    """Sec. III min-sum rule by its definition: min over j != i, product of signs over j != i."""
+    d = len(v)
+    out = []
+    for i in range(d):
+        others = [v[j] for j in range(d) if j != i]
+        mag = min(abs(x) for x in others)
+        neg = sum(1 for x in others if x < 0) % 2
+        m = corr(mag)
+        out.append(-m if neg else m)
+    return out
+
+
+@pytest.mark.parametrize("d", [2, 3, 5, 8, 10, 19])
+def test_check_node_f32_bruteforce(d):
+    rng = np.random.default_rng(d)
+    for trial in range(300):
+        if trial % 3 == 0:   # many ties and zeros
+            v = rng.integers(-3, 4, size=d).astype(np.float32)
+        else:
+            v = (rng.standard_normal(d) * 4).astype(np.float32)
+        for mode, corr in ((oracle.NORMALISED, lambda m: np.float32(0.75) * np.float32(m)),
+                           (oracle.OFFSET, lambda m: max(np.float32(m) - np.float32(0.5), np.float32(0)))):
+            got = oracle.check_node_f32(v, mode=mode, alpha=0.75, offset=0.5)
+            want = np.array(_cn_brute(v.tolist(), corr), np.float32)
+            assert np.array_equal(got, want), (v, got, want)
+        got = oracle.check_node_f32(v, mode=oracle.LEARNED, beta=1.25, gamma=0.5)
+        want = np.array(_cn_brute(v.tolist(), lambda m: np.float32(1.25) * max(np.float32(m) - np.float32(0.5), np.float32(0))), np.float32)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 8, 19])
+def test_check_node_i8_bruteforce(d):
+    rng = np.random.default_rng(100 + d)
+    for trial in range(500):
+        lim = 3 if trial % 2 else 127
+        v = rng.integers(-lim, lim + 1, size=d).astype(np.int8)
+        got = oracle.check_node_i8(v, offset_q=1)
+        want = _cn_brute([int(x) for x in v], lambda m: max(m - 1, 0))
+        assert got.tolist() == want
+
+
+def test_degree_two_is_scaled_copy():
+    """Degree-2 rows: min-sum equals sum-product; each output is beta times the other input."""
+    rng = np.random.default_rng(1)
+    for _ in range(100):
+        v = (rng.standard_normal(2) * 5).astype(np.float32)
+        out = oracle.check_node_f32(v, mode=oracle.NORMALISED, alpha=0.75)
+        assert out[0] == np.float32(0.75) * v[1] and out[1] == np.float32(0.75) * v[0]
+        w = v.astype(np.float64)
+        sp = [2 * np.arctanh(np.tanh(w[1] / 2)), 2 * np.arctanh(np.tanh(w[0] / 2))]
+        assert np.allclose(out / 0.75, sp, rtol=1e-4, atol=1e-5)
+
+
+def test_min_sum_magnitude_dominates_sum_product():
+    """|min-sum message| >= |sum-product message| before correction (textbook bound)."""
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        d = int(rng.integers(2, 12))
+        v = rng.standard_normal(d) * 3
+        ms = oracle.check_node_f32(v.astype(np.float32), mode=oracle.NORMALISED, alpha=1.0)
+        t = np.tanh(v / 2)
+        for i in range(d):
+            p = np.prod(np.delete(t, i))
+            sp = 2 * np.arctanh(np.clip(p, -1 + 1e-15, 1 - 1e-15))
+            assert abs(ms[i]) >= abs(sp) - 1e-5
+            assert np.sign(ms[i]) == np.sign(sp) or abs(sp) < 1e-6
+
+
+# ------------------------------------------------ exact results on a cycle-free code
+
+TREE_BASE = np.array([
+    # Z = 1, K_b = 4, 3 rows, columns 0..6; the Tanner graph is a chain (no cycles)
+    [0, 0, -1, -1, 0, -1, -1],
+    [-1, 0, 0, -1, -1, 0, -1],
+    [-1, -1, 0, 0, -1, -1, 0],
+], np.int16)
+
+
+def _tree_codebook():
+    H = (TREE_BASE >= 0).astype(np.int64)
+    words = np.array(list(itertools.product([0, 1], repeat=7)), np.int64)
+    return words[((H @ words.T) % 2 == 0).all(axis=0)]
+
+
+def test_tree_min_sum_equals_max_log():
+    """On a cycle-free graph min-sum (beta = 1) converges to the exact max-log bit LLRs:
+    L_j = min_{c: c_j=1} sum_k c_k L_k - min_{c: c_j=0} sum_k c_k L_k."""
+    C = _tree_codebook()
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        L = (rng.standard_normal(7) * 2).astype(np.float32)
+        cost = C @ L.astype(np.float64)
+        want = np.array([cost[C[:, j] == 1].min() - cost[C[:, j] == 0].min() for j in range(7)])
+        for dec in ("layered", "flooding"):
+            if dec == "layered":
+                r = oracle.decode_layered(TREE_BASE, 4, 1, 3, L[None, :], algo=oracle.NORMALISED,
+                                          alpha=1.0, max_iter=8, early_stop=False, punct=0,
+                                          want_post=True)
+            else:
+                r = oracle.decode_flooding(TREE_BASE, 4, 1, 3, L[None, :], algo=oracle.NORMALISED,
+                                           alpha=1.0, max_iter=8, early_stop=False, punct=0,
+                                           want_post=True)
+            assert np.allclose(r.post[0], want, atol=1e-4), (dec, r.post[0], want)
+
+
+def test_tree_sum_product_equals_map():
+    """Exact sum-product (flooding) on a cycle-free graph gives the exact bitwise MAP LLRs."""
+    C = _tree_codebook()
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        L = (rng.standard_normal(7) * 2).astype(np.float32)
+        w = np.exp(-(C @ L.astype(np.float64)))
+        want = np.array([np.log(w[C[:, j] == 0].sum()) - np.log(w[C[:, j] == 1].sum())
+                         for j in range(7)])
+        r = oracle.decode_flooding(TREE_BASE, 4, 1, 3, L[None, :], algo=oracle.SUM_PRODUCT,
+                                   max_iter=8, early_stop=False, punct=0, want_post=True)
+        assert np.allclose(r.post[0], want, atol=1e-4)
+
+
+# ----------------------------------------------------------------- P2: noiseless LLRs
+
+@pytest.mark.parametrize("kind,Z", [("BG1", 384), ("BG1", 16), ("BG2", 16), ("BG2", 128)])
+def test_noiseless_one_iteration(kind, Z):
+    for gseed in (0, 1, 2):
+        wl = make_workload(kind, Z, 3, 0.0, noiseless_llr=8.0, seed=5, graph_seed=gseed)
+        for llr, kw in ((wl.llr_int8(), dict(algo=oracle.OFFSET, offset_q=1)),
+                        (wl.llr, dict(algo=oracle.NORMALISED, alpha=0.75)),
+                        (wl.llr_fp16(), dict(algo=oracle.NORMALISED, alpha=0.75))):
+            r = oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, llr, max_iter=10, **kw)
+            assert (r.iters == 1).all()
+            assert (r.bits == wl.info).all()
+    q = wl.llr_int8()
+    assert (np.abs(q) == 32).all()
+
+
+# ------------------------------------------------------------ P4: brute-force ML decoding
+
+@pytest.mark.slow
+def test_tiny_code_matches_ml():
+    """K_b=3, 5 rows, Z=3, no puncturing: min-sum equals ML on >= 99% of frames at 7 dB."""
+    sh = SHAPES["TINY"]
+    Z = 3
+    base = generate_base_graph("TINY", 0)
+    K = sh.K_b * Z
+    allu = np.array(list(itertools.product([0, 1], repeat=K)), np.uint8)
+    book = encode_structured(base, sh.K_b, Z, allu).astype(np.float64)     # [512][24]
+    frames = 10000
+    wl = make_workload("TINY", Z, frames, 7.0, modulation="BPSK", seed=9, punct_cols=0, base=base)
+    cost = wl.llr.astype(np.float64) @ book.T                               # sum_{c_j=1} L_j
+    ml = allu[np.argmin(cost, axis=1)]                                      # lowest index on ties
+    r = oracle.decode_layered(base, sh.K_b, Z, sh.M, wl.llr, algo=oracle.NORMALISED, alpha=0.75,
+                              max_iter=20, punct=0)
+    agree = (r.bits == ml).all(axis=1).mean()
+    assert agree >= 0.99, agree
+
+
+# -------------------------------------------------------------- binary16 rounding
+
+def test_round_half_matches_ieee():
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([
+        rng.standard_normal(4000) * 10,
+        rng.standard_normal(1000) * 1e-5,                    # subnormal range
+        (rng.integers(-4096, 4096, 1000) + 0.5) / 2.0,        # ties
+        np.array([65504.0, 65519.0, 65520.0, -65520.0, 6.1e-5, 5.96e-8, 2.98e-8, 0.0])])
+    for x in xs:
+        with np.errstate(over="ignore"):
+            want = float(np.float16(np.float64(x)))
+        got = oracle.round_half(float(x))
+        assert got == want or (np.isinf(want) and np.isinf(got)), (x, got, want)
+
+
+# ------------------------------------------------------------ cross-mode identities
+
+def test_int8_equals_scaled_fp32_offset_without_saturation():
+    """With LLRs on the 1/4 grid and no saturation, int8 offset-1 decoding of q = 4L equals
+    4x the fp32 offset-0.25 decoding of L, message by message."""
+    wl = make_workload("BG1", 32, 6, 2.5, seed=2)
+    q = wl.llr_int8()
+    q = np.clip(q, -4, 4).astype(np.int8)           # small LLRs keep |L_v| below 127
+    L = q.astype(np.float32) / 4
+    for T in (1, 2):
+        ri = oracle.decode_layered(wl.base, wl.K_b, 32, wl.n_rows, q, algo=oracle.OFFSET,
+                                   offset_q=1, max_iter=T, early_stop=False, want_post=True,
+                                   want_c2v=True)
+        assert np.abs(ri.post.astype(int)).max() < 127
+        rf = oracle.decode_layered(wl.base, wl.K_b, 32, wl.n_rows, L, algo=oracle.OFFSET,
+                                   offset=0.25, max_iter=T, early_stop=False, want_post=True,
+                                   want_c2v=True)
+        assert np.array_equal(ri.post.astype(np.float32), 4 * rf.post)
+        assert np.array_equal(ri.c2v.astype(np.float32), 4 * rf.c2v)
+
+
+def test_fp16_close_to_fp32():
+    wl = make_workload("BG1", 64, 16, 2.0, seed=3)
+    r32 = oracle.decode_layered(wl.base, wl.K_b, 64, wl.n_rows, wl.llr, max_iter=5,
+                                early_stop=False, want_post=True)
+    r16 = oracle.decode_layered(wl.base, wl.K_b, 64, wl.n_rows, wl.llr_fp16(), max_iter=5,
+                                early_stop=False, want_post=True)
+    assert (r16.bits == r32.bits).mean() > 0.999
+    rel = np.abs(r16.post.astype(np.float32) - r32.post) / np.abs(r32.post).max()
+    assert np.median(rel) < 2 ** -7
+
+
+def test_early_stop_semantics():
+    wl = make_workload("BG2", 16, 40, 4.0, modulation="BPSK", seed=1)
+    ra = oracle.decode_layered(wl.base, wl.K_b, 16, wl.n_rows, wl.llr, max_iter=8,
+                               early_stop=True, want_post=True)
+    rb = oracle.decode_layered(wl.base, wl.K_b, 16, wl.n_rows, wl.llr, max_iter=8,
+                               early_stop=False)
+    assert (rb.iters == 8).all()
+    assert ((ra.iters >= 1) & (ra.iters <= 8)).all() and (ra.iters < 8).any()
+    # a codeword that stopped early has a zero syndrome on its hard decisions
+    hard = (ra.post < 0).astype(np.uint8)
+    for b in np.nonzero(ra.iters < 8)[0]:
+        assert oracle.syndrome_weight(wl.base, wl.K_b, 16, wl.n_rows, hard[b]) == 0
+    # and its result equals the fixed-iteration run stopped at that count
+    b = int(np.nonzero(ra.iters < 8)[0][0])
+    rc = oracle.decode_layered(wl.base, wl.K_b, 16, wl.n_rows, wl.llr[b:b + 1],
+                               max_iter=int(ra.iters[b]), early_stop=False, want_post=True)
+    assert np.array_equal(rc.post[0], ra.post[b])
+
+
+# ------------------------------------------------------------ P5 / P6: statistics
+
+@pytest.mark.slow
+def test_bler_monotone_in_ebn0():
+    bl = []
+    for eb in (0.0, 1.0, 2.0, 3.0):
+        wl = make_workload("BG2", 16, 200, eb, modulation="BPSK", seed=0)
+        r = oracle.decode_layered(wl.base, wl.K_b, 16, wl.n_rows, wl.llr, max_iter=8, threads=4)
+        bl.append((r.bits != wl.info).any(axis=1).mean())
+    assert all(bl[i + 1] <= bl[i] for i in range(3)), bl
+
+
+@pytest.mark.slow
+def test_layered_vs_flooding_iterations():
+    """Sec. III: layered needs about half the iterations of flooding.  Layered at T and
+    flooding at 2T are compared on bit errors at an operating point inside the waterfall."""
+    wl = make_workload("BG1", 64, 120, 2.0, seed=6)
+    lay = oracle.decode_layered(wl.base, wl.K_b, 64, wl.n_rows, wl.llr, max_iter=4, threads=4)
+    fl2 = oracle.decode_flooding(wl.base, wl.K_b, 64, wl.n_rows, wl.llr, max_iter=8, threads=4)
+    fl1 = oracle.decode_flooding(wl.base, wl.K_b, 64, wl.n_rows, wl.llr, max_iter=4, threads=4)
+    e_lay = (lay.bits != wl.info).mean()
+    e_fl2 = (fl2.bits != wl.info).mean()
+    e_fl1 = (fl1.bits != wl.info).mean()
+    assert e_lay < e_fl1                       # same iterations: layered is better
+    assert e_lay <= 3 * e_fl2 + 1e-3 and e_fl2 <= 3 * e_lay + 1e-3
