@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the layered min-sum decoder.
+
+Workload: seeded synthetic BG1-shaped graph (46 x 68, K_b = 22), Z = 384 (K = 8448),
+rate 1/3 (N_tx = 25344), QPSK over AWGN at Eb/N0 = 1.5 dB, int8 LLRs (scale 4, saturate
++-127), offset min-sum with offset 1, 10 iterations, batch 1024 codewords per GPU.  The
+headline runs a fixed 10 iterations (early stop off); a second measurement with early
+stop on is reported beside it.  One step = one decode of the whole batch (every step of
+the hot path: load, gather, v->c, check node, write-back, output).
+
+Metric: decoded information Gbit/s = batch * K / time, timed with CUDA events on the
+decode stream; inputs rotate over device copies totalling more than twice the L2 size, so
+no step reads its LLRs from L2.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+KIND, Z, EBN0, BATCH, T_ITER, SEED = "BG1", 384, 1.5, 1024, 10, 0
+WORKLOAD = "BG1-shaped 46x68 Z=384 K=8448 R=1/3 QPSK AWGN Eb/N0=1.5dB int8 offset-1 min-sum T=10"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_inputs(batch: int, rank: int, ebn0: float = EBN0):
+    from synth import make_workload
+    return make_workload(KIND, Z, batch, ebn0, modulation="QPSK", seed=SEED,
+                         first_cw=rank * batch)
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        import platform
+        return platform.machine()
+    except OSError:
+        return "unknown"
+
+
+def oracle_gbps(wl, q, seconds: float, threads: int):
+    """Decode the sample repeatedly with the CPU oracle for about `seconds`."""
+    import oracle
+    n = min(len(q), max(threads * 2, 16))
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, q[:n], algo=oracle.OFFSET,
+                              offset_q=1, max_iter=T_ITER, early_stop=False, threads=threads)
+        done += n
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return done * wl.K / el / 1e9, done, el
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: str):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch recorded from ncu in profiles/, if the kernel source still
+    matches the hash recorded beside it (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    src = os.path.join(ROOT, "paper_2009_05534_gb300", "csrc", "decode_layered.cu")
+    try:
+        text = open(path).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    got, sha = None, None
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            got = float(line.split(":", 1)[1].split()[0])
+        if line.startswith("kernel_source_sha256_16:"):
+            sha = line.split(":", 1)[1].strip()
+    return got if (got is not None and sha == h) else None
+
+
+# ----------------------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    threads = os.cpu_count() or 1
+    n = max(16, threads * 2)
+    wl = make_inputs(n, 0)
+    q = wl.llr_int8()
+    import oracle
+    for _ in range(args.warmup):
+        oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, q, algo=oracle.OFFSET,
+                              max_iter=T_ITER, early_stop=False, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, q, algo=oracle.OFFSET,
+                              max_iter=T_ITER, early_stop=False, threads=threads)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = n * wl.K * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": "decoded information throughput", "value": val,
+        "unit": "Gbit/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_step": n, "early_stop": False},
+        "cpu_baseline": {"value": val, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{n} codewords per step on {threads} threads "
+                                   f"({cpu_model()})"},
+        "e2e": {"value": val, "unit": "Gbit/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2009_05534_gb300 as ldpc
+    B = args.batch
+    wl = make_inputs(B, rank)
+    q = wl.llr_int8()
+    graph = ldpc.Graph(wl.base, wl.K_b, Z)
+    E = graph.edges()
+    stream = torch.cuda.Stream()
+    in_bytes = q.nbytes
+    n_copies = max(2, math.ceil(2.2 * L2_BYTES / in_bytes))
+    with torch.cuda.stream(stream):
+        host = torch.from_numpy(q)
+        bufs = [host.cuda(non_blocking=False) for _ in range(n_copies)]
+        nbytes = (wl.K + 7) // 8
+        bits = torch.empty((B, nbytes), dtype=torch.uint8, device="cuda")
+        iters = torch.empty((B,), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(k, early_stop=False, buf=None):
+        ldpc.decode(graph, bufs[k % n_copies] if buf is None else buf, T_ITER, bits=bits,
+                    iters=iters, stream=stream, early_stop=early_stop)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    graph.sync_status(stream)
+    # correctness spot check against the LLRs' own decode stays in the test-suite
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    idx = vis.split(",")[local] if vis else str(local)
+    sampler = ClockSampler(idx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    l0 = ldpc.launch_count()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step(k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = ldpc.launch_count() - l0
+    barrier()
+    clocks = sampler.stop()
+    graph.sync_status(stream)
+    per = [a.elapsed_time(b) / 1e3 for a, b in ev]         # seconds per step (= per launch)
+    elapsed = ev[0][0].elapsed_time(ev[-1][1]) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    bits_total = world * args.steps * B * wl.K
+    value = bits_total / elapsed / 1e9
+    kern = sum(per) / len(per)
+
+    # early stop on (same data, 10-iteration cap): mean iterations and throughput
+    es_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    es_ev[0].record(stream)
+    for k in range(args.steps):
+        step(k, early_stop=True)
+    es_ev[1].record(stream)
+    torch.cuda.synchronize()
+    es_time = es_ev[0].elapsed_time(es_ev[1]) / 1e3
+    mean_it = float(iters.float().mean().item())
+    es_gbps = args.steps * B * wl.K / es_time / 1e9
+
+    # end to end through the host-buffer C-ABI call (pinned memory, copies timed)
+    pin = torch.from_numpy(q).pin_memory()
+    hbits = torch.empty((B, nbytes), dtype=torch.uint8).pin_memory()
+    hit = torch.empty((B,), dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        ldpc.decode_host(graph, pin, T_ITER, bits=hbits, iters=hit, stream=stream,
+                         early_stop=False)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ldpc.decode_host(graph, pin, T_ITER, bits=hbits, iters=hit, stream=stream,
+                         early_stop=False)
+    e2e_t = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = world * args.steps * B * wl.K / e2e_t / 1e9
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    f_max = (peaks or {}).get("sm_max_mhz") or 2070.0
+    edge_updates = T_ITER * E * Z * B
+    alu_peak = n_sm * f_max * 1e6 * 512.0 / 12.0            # edge updates / s (int8x4 issue)
+    achieved = edge_updates / kern
+    hbm_peak = (peaks or {}).get("hbm_gbs")
+    alg_bytes = B * (wl.n_tx + nbytes + 4)
+    traffic = profiled_traffic("layered_int8_bg1_z384")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        g, done, el = oracle_gbps(wl, q, 12.0, threads)
+        cpu = {"value": g, "unit": "Gbit/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {min(len(q), max(threads * 2, 16))} codewords of the batch, "
+                         f"decoded repeatedly ({done} codewords in {el:.1f} s, {cpu_model()})"}
+    if rank == 0:
+        line = {
+            "metric": "decoded information throughput (BG1 Z=384, 10 it)",
+            "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_per_gpu": B, "E": E, "n_tx": wl.n_tx,
+                       "early_stop": False, "l2": f"inputs rotate over {n_copies} device "
+                                                   f"copies ({n_copies * in_bytes / 2**20:.0f} MiB > L2)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": alu_peak / 1e9,
+                         "unit": "Gedge/s", "frac": achieved / alu_peak,
+                         "traffic": traffic,
+                         "peak_basis": f"{n_sm} SMs x {f_max:.0f} MHz x 512/12 edge updates "
+                                       "per SM per clock (int8x4 issue, 12 lane-ops/edge)",
+                         "algorithmic_bytes": alg_bytes,
+                         "hbm_frac": (alg_bytes / kern / 1e9 / hbm_peak) if hbm_peak else None,
+                         "kernel_ms": 1e3 * kern},
+            "early_stop": {"value": es_gbps, "unit": "Gbit/s", "mean_iterations": mean_it,
+                           "ebn0_db": EBN0},
+            "e2e": {"value": e2e, "unit": "Gbit/s", "h2d_bytes_per_step": in_bytes,
+                    "d2h_bytes_per_step": B * (nbytes + 4)},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "wall_s": t_wall,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    graph.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

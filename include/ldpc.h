@@ -1,0 +1,157 @@
+/*
+ * ldpc.h — C ABI of the GB300 (sm_103a) layered min-sum LDPC decoder.
+ *
+ * The interface follows the paper's statement of the problem (Ling & Cautereels, "Fast
+ * LDPC GPU Decoder for Cloud RAN"):
+ *   Sec. II   a quasi-cyclic code is a base graph H_BG (M_bg x N_bg, K_b systematic
+ *             columns) lifted by Z; rate is chosen by the number of base rows used; the
+ *             first two information columns are punctured.
+ *   Sec. III  the decoder consumes the demapper's bit LLRs L_b, iterates layered min-sum
+ *             (check rule with a correction, posterior update, next message) and stops at
+ *             a valid codeword or at the iteration cap.
+ *   Sec. IV   many codewords are decoded in parallel across the GPU.
+ *
+ * Conventions
+ *   - LLR = ln P(b=0)/P(b=1); hard decision bit = (L_v < 0); sgn(0) = +1.
+ *   - Circulant shift: entry V >= 0 of the base table gives shift s = V mod Z; check row i
+ *     of block (r, c) connects variable c*Z + ((i + s) mod Z).  -1 marks a zero block.
+ *   - Channel LLRs of one codeword cover codeword positions [punct_cols*Z,
+ *     punct_cols*Z + n_tx); every other used position starts at LLR 0.
+ *   - Hard bits: the K = K_b*Z information bits (punctured ones included), packed
+ *     LSB-first: bit j is bit (j & 7) of byte (j >> 3); ceil(K/8) bytes per codeword.
+ *   - All device buffers are owned by the caller; the graph owns its own device tables.
+ *   - Calls are asynchronous on `stream`: argument errors found on the host are returned
+ *     at once; errors raised inside a kernel are written to the graph's device status word
+ *     and returned by ldpc_graph_sync_status.
+ *   - No exceptions cross this interface.  A graph may be used by several host threads
+ *     for decodes on different streams at the same time.
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ldpc_graph *ldpc_graph_t;       /* opaque, device-resident tables */
+typedef struct CUstream_st *ldpc_stream_t;     /* same type as cudaStream_t */
+
+typedef enum {
+    LDPC_OK = 0,
+    LDPC_ERR_INVALID_ARG = 1,
+    LDPC_ERR_UNSUPPORTED = 2,
+    LDPC_ERR_OUT_OF_MEMORY = 3,
+    LDPC_ERR_CUDA = 4,
+    LDPC_ERR_TIMEOUT = 5
+} ldpc_status;
+
+typedef enum { LDPC_LLR_INT8 = 0, LDPC_LLR_FP16 = 1, LDPC_LLR_FP32 = 2 } ldpc_llr_type;
+typedef enum { LDPC_NORMALISED = 0, LDPC_OFFSET = 1, LDPC_LEARNED = 2 } ldpc_algo;
+
+/* Decoder options.  Fill with ldpc_decode_opts_default() and change what you need.
+ *   llr_type     element type of the channel LLRs, posteriors and messages.
+ *   algo         check-node correction (Sec. III, the factor beta):
+ *                  LDPC_NORMALISED  m' = alpha * m            (fp16 / fp32)
+ *                  LDPC_OFFSET      m' = max(m - offset, 0)   (int8: offset_q LLR units)
+ *                  LDPC_LEARNED     m' = beta[t][r] * max(m - gamma[t][r], 0)
+ *   alpha        normalisation factor (default 0.75).
+ *   offset       offset for fp16 / fp32 in LLR units (default 0).
+ *   offset_q     offset for int8 in quantised units (default 1).
+ *   n_rows       base rows used, 4 <= n_rows <= M_bg; 0 = all rows (rate, Sec. II).
+ *   n_tx         channel LLRs per codeword; 0 = (K_b + n_rows - punct_cols) * Z.
+ *   punct_cols   punctured leading columns (default 2, Sec. II).
+ *   early_stop   1: stop a codeword when its syndrome is zero after a full iteration.
+ *   cluster_size 1 (one thread block per codeword; other values are reserved).
+ *   learned_params device float [max_iter][n_rows][2] = (beta, gamma) for LDPC_LEARNED. */
+typedef struct {
+    int llr_type;
+    int algo;
+    float alpha;
+    float offset;
+    int offset_q;
+    int n_rows;
+    int n_tx;
+    int punct_cols;
+    int early_stop;
+    int cluster_size;
+    const float *learned_params;
+} ldpc_decode_opts;
+
+/* Defaults: int8, offset min-sum with offset_q = 1, alpha = 0.75, all rows, n_tx from the
+ * rows, punct_cols = 2, early_stop = 1, cluster_size = 1, no learned table. */
+void ldpc_decode_opts_default(ldpc_decode_opts *opts);
+
+/* Build a device-resident graph from a host base table (Sec. II).
+ *   base_shift  host int16 [M_bg][N_bg], row-major; -1 = zero block, V >= 0 a circulant
+ *               with shift V mod Z.  The table is copied; the caller keeps ownership.
+ *               A decode that uses n_rows rows requires every non-zero entry of those
+ *               rows to lie in a column < K_b + n_rows (checked per call).
+ *   M_bg, N_bg  1 <= M_bg <= 64, 2 <= N_bg <= 128;  K_b >= 1;  1 <= Z <= 1024.
+ *   out         receives the handle.
+ * Returns LDPC_ERR_INVALID_ARG for bad shapes or values, LDPC_ERR_OUT_OF_MEMORY /
+ * LDPC_ERR_CUDA if the device tables cannot be allocated or copied.  Synchronous. */
+ldpc_status ldpc_graph_create(const int16_t *base_shift, int M_bg, int N_bg, int K_b, int Z,
+                              ldpc_graph_t *out);
+
+/* Release a graph (waits for the device to finish with it). */
+ldpc_status ldpc_graph_destroy(ldpc_graph_t g);
+
+/* Shape queries: edges (non-zero circulants) in the first n_rows rows (0 = all), and the
+ * number of posterior entries (K_b + n_rows) * Z.  Return -1 on a bad argument. */
+int ldpc_graph_edges(ldpc_graph_t g, int n_rows);
+int ldpc_graph_vars(ldpc_graph_t g, int n_rows);
+
+/* Decode a batch (Sec. III layered min-sum, Sec. IV batch parallel).
+ *   llr_dev        device [batch][n_tx] of int8 / binary16 / float32 per opts->llr_type.
+ *   batch          codewords (>= 0; 0 is a no-op).
+ *   max_iter       iteration cap T, 1..64.
+ *   stream         CUDA stream (NULL = legacy default stream).
+ *   opts           NULL = defaults.
+ *   hard_bits_dev  device uint8 [batch][ceil(K/8)] output.
+ *   iters_dev      device int32 [batch] output: iterations executed (T without early stop).
+ * Host-side argument errors return at once and launch nothing.  Returns after the launch. */
+ldpc_status ldpc_decode(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
+                        ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                        uint8_t *hard_bits_dev, int32_t *iters_dev);
+
+/* As ldpc_decode, and also writes the final posteriors and check-to-variable messages
+ * (for parity tests):
+ *   post_dev  device [batch][(K_b + n_rows) * Z] in the LLR type.
+ *   c2v_dev   device [batch][E * Z] in the LLR type, edge-major: the message of edge e
+ *             (edges ordered by row, then column) on check row i is at e*Z + i.
+ * Either may be NULL. */
+ldpc_status ldpc_decode_debug(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
+                              ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                              uint8_t *hard_bits_dev, int32_t *iters_dev, void *post_dev,
+                              void *c2v_dev);
+
+/* Host-buffer variant for callers whose data lives in host memory.
+ *   llr_host        host [batch][n_tx] in the LLR type (pinned memory gives the fastest
+ *                   copies; pageable memory works).
+ *   hard_bits_host  host uint8 [batch][ceil(K/8)];  iters_host  host int32 [batch].
+ * The graph keeps device staging buffers (grown on demand, reused across calls); the call
+ * copies the LLRs in, decodes, copies the results out on `stream`, and returns after the
+ * results are in host memory.  Calls on the same graph from several threads are
+ * serialised.  LDPC_ERR_OUT_OF_MEMORY if the staging buffers cannot be allocated. */
+ldpc_status ldpc_decode_host(ldpc_graph_t g, const void *llr_host, int batch, int max_iter,
+                             ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                             uint8_t *hard_bits_host, int32_t *iters_host);
+
+/* Wait for the graph's outstanding work on `stream` and return (then clear) the device
+ * status word: LDPC_OK, or the first error a kernel reported (e.g. LDPC_ERR_TIMEOUT). */
+ldpc_status ldpc_graph_sync_status(ldpc_graph_t g, ldpc_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char *ldpc_status_string(ldpc_status s);
+
+/* Number of kernels this library has launched since it was loaded (all threads). */
+uint64_t ldpc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_GB300_H */

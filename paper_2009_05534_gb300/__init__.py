@@ -1,0 +1,241 @@
+"""GB300-native layered min-sum LDPC decoder (Ling & Cautereels, "Fast LDPC GPU Decoder for
+Cloud RAN").
+
+Thin Python binding over the C ABI declared in ``include/ldpc.h`` (``libldpc.so`` next to
+this file).  It only marshals arguments: torch supplies device buffers and the current
+CUDA stream, and every step of decoding runs in the library's CUDA kernels.  There is no
+CPU fallback: if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libldpc.so")
+
+LLR_INT8, LLR_FP16, LLR_FP32 = 0, 1, 2
+NORMALISED, OFFSET, LEARNED = 0, 1, 2
+
+_STATUS = {0: "LDPC_OK", 1: "LDPC_ERR_INVALID_ARG", 2: "LDPC_ERR_UNSUPPORTED",
+           3: "LDPC_ERR_OUT_OF_MEMORY", 4: "LDPC_ERR_CUDA", 5: "LDPC_ERR_TIMEOUT"}
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {_STATUS.get(status, status)}")
+        self.status = status
+
+
+class DecodeOpts(ctypes.Structure):
+    _fields_ = [("llr_type", ctypes.c_int), ("algo", ctypes.c_int), ("alpha", ctypes.c_float),
+                ("offset", ctypes.c_float), ("offset_q", ctypes.c_int), ("n_rows", ctypes.c_int),
+                ("n_tx", ctypes.c_int), ("punct_cols", ctypes.c_int),
+                ("early_stop", ctypes.c_int), ("cluster_size", ctypes.c_int),
+                ("learned_params", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# exported symbols of the C ABI (checked by the CPU test-suite against include/ldpc.h)
+ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_destroy",
+               "ldpc_graph_edges", "ldpc_graph_vars", "ldpc_decode", "ldpc_decode_debug",
+               "ldpc_graph_sync_status", "ldpc_status_string", "ldpc_launch_count",
+               "ldpc_decode_host")
+
+
+def lib():
+    """Load libldpc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i = ctypes.c_void_p, ctypes.c_int
+            L.ldpc_decode_opts_default.argtypes = [ctypes.POINTER(DecodeOpts)]
+            L.ldpc_decode_opts_default.restype = None
+            L.ldpc_graph_create.argtypes = [P, i, i, i, i, ctypes.POINTER(ctypes.c_void_p)]
+            L.ldpc_graph_create.restype = i
+            L.ldpc_graph_destroy.argtypes = [P]
+            L.ldpc_graph_destroy.restype = i
+            L.ldpc_graph_edges.argtypes = [P, i]
+            L.ldpc_graph_edges.restype = i
+            L.ldpc_graph_vars.argtypes = [P, i]
+            L.ldpc_graph_vars.restype = i
+            L.ldpc_decode.argtypes = [P, P, i, i, P, ctypes.POINTER(DecodeOpts), P, P]
+            L.ldpc_decode.restype = i
+            L.ldpc_decode_debug.argtypes = [P, P, i, i, P, ctypes.POINTER(DecodeOpts), P, P,
+                                            P, P]
+            L.ldpc_decode_debug.restype = i
+            L.ldpc_decode_host.argtypes = [P, P, i, i, P, ctypes.POINTER(DecodeOpts), P, P]
+            L.ldpc_decode_host.restype = i
+            L.ldpc_graph_sync_status.argtypes = [P, P]
+            L.ldpc_graph_sync_status.restype = i
+            L.ldpc_status_string.argtypes = [i]
+            L.ldpc_status_string.restype = ctypes.c_char_p
+            L.ldpc_launch_count.argtypes = []
+            L.ldpc_launch_count.restype = ctypes.c_uint64
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise LdpcError(st, what)
+
+
+def launch_count() -> int:
+    """Kernels launched by libldpc.so since it was loaded."""
+    return int(lib().ldpc_launch_count())
+
+
+class Graph:
+    """Device-resident QC base graph lifted by Z (ldpc_graph_create)."""
+
+    def __init__(self, base: np.ndarray, K_b: int, Z: int):
+        b = np.ascontiguousarray(base, dtype=np.int16)
+        if b.ndim != 2:
+            raise ValueError("base table must be 2-D [M_bg][N_bg]")
+        h = ctypes.c_void_p()
+        _check(lib().ldpc_graph_create(b.ctypes.data_as(ctypes.c_void_p), b.shape[0],
+                                       b.shape[1], int(K_b), int(Z), ctypes.byref(h)),
+               "ldpc_graph_create")
+        self._h = h
+        self.M_bg, self.N_bg = b.shape
+        self.K_b, self.Z = int(K_b), int(Z)
+        self.base = b.copy()
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("graph is closed")
+        return self._h
+
+    @property
+    def K(self) -> int:
+        return self.K_b * self.Z
+
+    def edges(self, n_rows: int = 0) -> int:
+        return int(lib().ldpc_graph_edges(self.handle, int(n_rows)))
+
+    def vars(self, n_rows: int = 0) -> int:
+        return int(lib().ldpc_graph_vars(self.handle, int(n_rows)))
+
+    def sync_status(self, stream=None):
+        _check(lib().ldpc_graph_sync_status(self.handle, _stream_ptr(stream)), "device status")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().ldpc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_opts(llr_type: int, *, algo=None, alpha=0.75, offset=0.0, offset_q=1, n_rows=0,
+              n_tx=0, punct_cols=2, early_stop=True, learned=None) -> DecodeOpts:
+    o = DecodeOpts()
+    lib().ldpc_decode_opts_default(ctypes.byref(o))
+    o.llr_type = llr_type
+    o.algo = (OFFSET if llr_type == LLR_INT8 else NORMALISED) if algo is None else algo
+    o.alpha = alpha
+    o.offset = offset
+    o.offset_q = offset_q
+    o.n_rows = n_rows
+    o.n_tx = n_tx
+    o.punct_cols = punct_cols
+    o.early_stop = int(bool(early_stop))
+    o.learned_params = None if learned is None else learned.data_ptr()
+    return o
+
+
+def _llr_type(t) -> int:
+    import torch
+    m = {torch.int8: LLR_INT8, torch.float16: LLR_FP16, torch.float32: LLR_FP32}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported LLR dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def decode(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stream=None,
+           debug: bool = False, **kw):
+    """Decode llr [batch][n_tx] (a CUDA tensor of int8 / float16 / float32).
+
+    Returns (bits uint8 [batch][ceil(K/8)], iters int32 [batch]) and, with debug=True,
+    also (posteriors [batch][vars], c2v [batch][E*Z]) in the LLR dtype.
+    """
+    import torch
+    if not llr.is_cuda:
+        raise ValueError("llr must be a CUDA tensor")
+    llr = llr.contiguous()
+    B = llr.shape[0]
+    lt = _llr_type(llr)
+    o = make_opts(lt, **kw)
+    nb = (graph.K + 7) // 8
+    dev = llr.device
+    if bits is None:
+        bits = torch.empty((B, nb), dtype=torch.uint8, device=dev)
+    if iters is None:
+        iters = torch.empty((B,), dtype=torch.int32, device=dev)
+    sp = _stream_ptr(stream)
+    if not debug:
+        _check(lib().ldpc_decode(graph.handle, ctypes.c_void_p(llr.data_ptr()), B, int(max_iter),
+                                 sp, ctypes.byref(o), ctypes.c_void_p(bits.data_ptr()),
+                                 ctypes.c_void_p(iters.data_ptr())), "ldpc_decode")
+        return bits, iters
+    n_rows = kw.get("n_rows", 0)
+    post = torch.empty((B, graph.vars(n_rows)), dtype=llr.dtype, device=dev)
+    c2v = torch.empty((B, graph.edges(n_rows) * graph.Z), dtype=llr.dtype, device=dev)
+    _check(lib().ldpc_decode_debug(graph.handle, ctypes.c_void_p(llr.data_ptr()), B,
+                                   int(max_iter), sp, ctypes.byref(o),
+                                   ctypes.c_void_p(bits.data_ptr()),
+                                   ctypes.c_void_p(iters.data_ptr()),
+                                   ctypes.c_void_p(post.data_ptr()),
+                                   ctypes.c_void_p(c2v.data_ptr())), "ldpc_decode_debug")
+    return bits, iters, post, c2v
+
+
+def decode_host(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stream=None,
+                **kw):
+    """Decode host LLRs (a CPU tensor or numpy array, pinned memory preferred) through
+    ldpc_decode_host; returns host (bits uint8 [batch][ceil(K/8)], iters int32 [batch])."""
+    import torch
+    if isinstance(llr, np.ndarray):
+        llr = torch.from_numpy(np.ascontiguousarray(llr))
+    if llr.is_cuda:
+        raise ValueError("decode_host takes host memory")
+    llr = llr.contiguous()
+    B = llr.shape[0]
+    o = make_opts(_llr_type(llr), **kw)
+    nb = (graph.K + 7) // 8
+    if bits is None:
+        bits = torch.empty((B, nb), dtype=torch.uint8)
+    if iters is None:
+        iters = torch.empty((B,), dtype=torch.int32)
+    _check(lib().ldpc_decode_host(graph.handle, ctypes.c_void_p(llr.data_ptr()), B,
+                                  int(max_iter), _stream_ptr(stream), ctypes.byref(o),
+                                  ctypes.c_void_p(bits.data_ptr()),
+                                  ctypes.c_void_p(iters.data_ptr())), "ldpc_decode_host")
+    return bits, iters
+
+
+def unpack_bits(packed: np.ndarray, K: int) -> np.ndarray:
+    """LSB-first packed hard bits [B][ceil(K/8)] -> uint8 [B][K]."""
+    return np.unpackbits(np.asarray(packed, dtype=np.uint8), axis=1, bitorder="little")[:, :K]

@@ -1,0 +1,292 @@
+// C-ABI entry points: graph construction (paper Sec. II code model) and the decode calls
+// (Sec. III layered min-sum over a batch, Sec. IV).  Host-side validation only; all
+// decoding work runs in the kernels of decode_layered.cu.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ldpc_internal.h"
+
+namespace ldpc {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace ldpc
+
+using ldpc::Graph;
+
+extern "C" {
+
+void ldpc_decode_opts_default(ldpc_decode_opts *o) {
+    if (!o) return;
+    o->llr_type = LDPC_LLR_INT8;
+    o->algo = LDPC_OFFSET;
+    o->alpha = 0.75f;
+    o->offset = 0.0f;
+    o->offset_q = 1;
+    o->n_rows = 0;
+    o->n_tx = 0;
+    o->punct_cols = 2;
+    o->early_stop = 1;
+    o->cluster_size = 1;
+    o->learned_params = nullptr;
+}
+
+const char *ldpc_status_string(ldpc_status s) {
+    switch (s) {
+    case LDPC_OK: return "LDPC_OK";
+    case LDPC_ERR_INVALID_ARG: return "LDPC_ERR_INVALID_ARG";
+    case LDPC_ERR_UNSUPPORTED: return "LDPC_ERR_UNSUPPORTED";
+    case LDPC_ERR_OUT_OF_MEMORY: return "LDPC_ERR_OUT_OF_MEMORY";
+    case LDPC_ERR_CUDA: return "LDPC_ERR_CUDA";
+    case LDPC_ERR_TIMEOUT: return "LDPC_ERR_TIMEOUT";
+    }
+    return "LDPC_ERR_UNKNOWN";
+}
+
+uint64_t ldpc_launch_count(void) { return ldpc::g_launches.load(); }
+
+ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, int Z,
+                              ldpc_graph_t *out) {
+    if (!out) return LDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!base || M_bg < 1 || M_bg > ldpc::kMaxRows || N_bg < 2 || N_bg > ldpc::kMaxCols ||
+        K_b < 1 || K_b >= N_bg || Z < 1 || Z > ldpc::kMaxZ)
+        return LDPC_ERR_INVALID_ARG;
+    int E = 0;
+    for (int k = 0; k < M_bg * N_bg; ++k) {
+        if (base[k] < -1) return LDPC_ERR_INVALID_ARG;
+        if (base[k] >= 0) ++E;
+    }
+    if (E == 0) return LDPC_ERR_INVALID_ARG;
+    Graph *g = new (std::nothrow) Graph;
+    if (!g) return LDPC_ERR_OUT_OF_MEMORY;
+    g->M_bg = M_bg;
+    g->N_bg = N_bg;
+    g->K_b = K_b;
+    g->Z = Z;
+    g->E_total = E;
+    uint32_t *h_edges = (uint32_t *)std::malloc(sizeof(uint32_t) * E);
+    if (!h_edges) {
+        delete g;
+        return LDPC_ERR_OUT_OF_MEMORY;
+    }
+    int e = 0, maxc = -1, maxd = 0;
+    for (int r = 0; r < M_bg; ++r) {
+        g->row_ptr[r] = e;
+        g->max_col_upto[r] = maxc;
+        g->max_deg_upto[r] = maxd;
+        int d = 0;
+        for (int c = 0; c < N_bg; ++c) {
+            const int v = base[r * N_bg + c];
+            if (v < 0) continue;
+            h_edges[e++] = ((uint32_t)c << 16) | (uint32_t)(v % Z);
+            if (c > maxc) maxc = c;
+            ++d;
+        }
+        if (d > maxd) maxd = d;
+    }
+    g->row_ptr[M_bg] = e;
+    g->max_col_upto[M_bg] = maxc;
+    g->max_deg_upto[M_bg] = maxd;
+    cudaGetDevice(&g->device);
+    ldpc_status st = LDPC_OK;
+    if (cudaMalloc(&g->d_edges, sizeof(uint32_t) * E) != cudaSuccess ||
+        cudaMalloc(&g->d_row_ptr, sizeof(int) * (M_bg + 1)) != cudaSuccess ||
+        cudaMalloc(&g->d_status, sizeof(int)) != cudaSuccess) {
+        st = LDPC_ERR_OUT_OF_MEMORY;
+    } else if (cudaMemcpy(g->d_edges, h_edges, sizeof(uint32_t) * E, cudaMemcpyHostToDevice) !=
+                   cudaSuccess ||
+               cudaMemcpy(g->d_row_ptr, g->row_ptr, sizeof(int) * (M_bg + 1),
+                          cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemset(g->d_status, 0, sizeof(int)) != cudaSuccess) {
+        st = LDPC_ERR_CUDA;
+    }
+    std::free(h_edges);
+    if (st != LDPC_OK) {
+        cudaGetLastError();
+        cudaFree(g->d_edges);
+        cudaFree(g->d_row_ptr);
+        cudaFree(g->d_status);
+        delete g;
+        return st;
+    }
+    *out = reinterpret_cast<ldpc_graph_t>(g);
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_graph_destroy(ldpc_graph_t h) {
+    if (!h) return LDPC_ERR_INVALID_ARG;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    cudaDeviceSynchronize();
+    cudaFree(g->d_edges);
+    cudaFree(g->d_row_ptr);
+    cudaFree(g->d_status);
+    cudaFree(g->d_stage);
+    delete g;
+    return LDPC_OK;
+}
+
+int ldpc_graph_edges(ldpc_graph_t h, int n_rows) {
+    if (!h) return -1;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    if (n_rows == 0) n_rows = g->M_bg;
+    if (n_rows < 1 || n_rows > g->M_bg) return -1;
+    return g->row_ptr[n_rows];
+}
+
+int ldpc_graph_vars(ldpc_graph_t h, int n_rows) {
+    if (!h) return -1;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    if (n_rows == 0) n_rows = g->M_bg;
+    if (n_rows < 1 || n_rows > g->M_bg) return -1;
+    return (g->K_b + n_rows) * g->Z;
+}
+
+static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int max_iter,
+                                 ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                                 uint8_t *bits, int32_t *iters, void *post, void *c2v) {
+    if (!h) return LDPC_ERR_INVALID_ARG;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    ldpc_decode_opts o;
+    if (opts)
+        o = *opts;
+    else
+        ldpc_decode_opts_default(&o);
+    if (batch < 0 || max_iter < 1 || max_iter > ldpc::kMaxIter) return LDPC_ERR_INVALID_ARG;
+    if (o.llr_type < LDPC_LLR_INT8 || o.llr_type > LDPC_LLR_FP32) return LDPC_ERR_INVALID_ARG;
+    if (o.algo < LDPC_NORMALISED || o.algo > LDPC_LEARNED) return LDPC_ERR_INVALID_ARG;
+    if (o.llr_type == LDPC_LLR_INT8 && o.algo != LDPC_OFFSET) return LDPC_ERR_UNSUPPORTED;
+    if (o.algo == LDPC_LEARNED && !o.learned_params) return LDPC_ERR_INVALID_ARG;
+    if (o.cluster_size != 1) return LDPC_ERR_UNSUPPORTED;
+    const int n_rows = o.n_rows == 0 ? g->M_bg : o.n_rows;
+    if (n_rows < 1 || n_rows > g->M_bg) return LDPC_ERR_INVALID_ARG;
+    const int n_cols = g->K_b + n_rows;
+    if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
+    if (o.punct_cols < 0 || o.punct_cols > n_cols) return LDPC_ERR_INVALID_ARG;
+    const int n_tx = o.n_tx == 0 ? (n_cols - o.punct_cols) * g->Z : o.n_tx;
+    if (n_tx < 0 || o.punct_cols * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+    if (batch == 0) return LDPC_OK;
+    if (!llr || !bits || !iters) return LDPC_ERR_INVALID_ARG;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != g->device) return LDPC_ERR_INVALID_ARG;
+
+    ldpc::DecodeParams p;
+    p.edges = g->d_edges;
+    p.row_ptr = g->d_row_ptr;
+    p.n_rows = n_rows;
+    p.E = g->row_ptr[n_rows];
+    p.Z = g->Z;
+    p.n_cols = n_cols;
+    p.K_b = g->K_b;
+    p.punct = o.punct_cols;
+    p.n_tx = n_tx;
+    p.max_iter = max_iter;
+    p.early_stop = o.early_stop ? 1 : 0;
+    p.batch = batch;
+    p.algo = o.algo;
+    p.alpha = o.alpha;
+    p.offset = o.offset;
+    p.offset_q = o.offset_q;
+    p.learned = o.learned_params;
+    p.llr = llr;
+    p.bits = bits;
+    p.iters = iters;
+    p.post = post;
+    p.c2v = c2v;
+    p.status = g->d_status;
+    return ldpc::launch_layered(p, o.llr_type, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ldpc_status ldpc_decode(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
+                        ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                        uint8_t *hard_bits_dev, int32_t *iters_dev) {
+    return decode_common(g, llr_dev, batch, max_iter, stream, opts, hard_bits_dev, iters_dev,
+                         nullptr, nullptr);
+}
+
+ldpc_status ldpc_decode_debug(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
+                              ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                              uint8_t *hard_bits_dev, int32_t *iters_dev, void *post_dev,
+                              void *c2v_dev) {
+    return decode_common(g, llr_dev, batch, max_iter, stream, opts, hard_bits_dev, iters_dev,
+                         post_dev, c2v_dev);
+}
+
+ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, int max_iter,
+                             ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                             uint8_t *hard_bits_host, int32_t *iters_host) {
+    if (!h) return LDPC_ERR_INVALID_ARG;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    ldpc_decode_opts o;
+    if (opts)
+        o = *opts;
+    else
+        ldpc_decode_opts_default(&o);
+    if (batch < 0) return LDPC_ERR_INVALID_ARG;
+    if (batch == 0) return LDPC_OK;
+    if (!llr_host || !hard_bits_host || !iters_host) return LDPC_ERR_INVALID_ARG;
+    const int n_rows = o.n_rows == 0 ? g->M_bg : o.n_rows;
+    if (n_rows < 1 || n_rows > g->M_bg || o.punct_cols < 0) return LDPC_ERR_INVALID_ARG;
+    const int n_cols = g->K_b + n_rows;
+    const int n_tx = o.n_tx == 0 ? (n_cols - o.punct_cols) * g->Z : o.n_tx;
+    if (n_tx < 0) return LDPC_ERR_INVALID_ARG;
+    const size_t esz = o.llr_type == LDPC_LLR_INT8 ? 1 : (o.llr_type == LDPC_LLR_FP16 ? 2 : 4);
+    const size_t nbytes = (size_t)(g->K_b * g->Z + 7) / 8;
+    const size_t in_b = (size_t)batch * n_tx * esz;
+    const size_t bits_b = (size_t)batch * nbytes;
+    const size_t it_b = (size_t)batch * sizeof(int32_t);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t need = up(in_b) + up(bits_b) + up(it_b);
+    std::lock_guard<std::mutex> lk(g->host_mu);
+    if (need > g->stage_bytes) {
+        cudaFree(g->d_stage);
+        g->d_stage = nullptr;
+        g->stage_bytes = 0;
+        if (cudaMalloc(&g->d_stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return LDPC_ERR_OUT_OF_MEMORY;
+        }
+        g->stage_bytes = need;
+    }
+    char *base = (char *)g->d_stage;
+    void *d_llr = base;
+    uint8_t *d_bits = (uint8_t *)(base + up(in_b));
+    int32_t *d_it = (int32_t *)(base + up(in_b) + up(bits_b));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(d_llr, llr_host, in_b, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    ldpc_status st = decode_common(h, d_llr, batch, max_iter, stream, &o, d_bits, d_it,
+                                   nullptr, nullptr);
+    if (st != LDPC_OK) {
+        cudaStreamSynchronize(s);
+        return st;
+    }
+    if (cudaMemcpyAsync(hard_bits_host, d_bits, bits_b, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(iters_host, d_it, it_b, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_graph_sync_status(ldpc_graph_t h, ldpc_stream_t stream) {
+    if (!h) return LDPC_ERR_INVALID_ARG;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int v = 0;
+    if (cudaMemcpyAsync(&v, g->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    if (v != 0) {
+        if (cudaMemsetAsync(g->d_status, 0, sizeof(int), s) != cudaSuccess) return LDPC_ERR_CUDA;
+        cudaStreamSynchronize(s);
+    }
+    return (ldpc_status)v;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Internal definitions shared by the C-ABI entry points and the decoder kernels.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <cuda_runtime.h>
+
+#include "../../include/ldpc.h"
+
+namespace ldpc {
+
+constexpr int kMaxRows = 64;
+constexpr int kMaxCols = 128;
+constexpr int kMaxZ = 1024;
+constexpr int kMaxIter = 64;
+
+// Host-side graph object behind ldpc_graph_t.
+struct Graph {
+    int M_bg = 0, N_bg = 0, K_b = 0, Z = 0;
+    int E_total = 0;
+    int row_ptr[kMaxRows + 1] = {};      // edges of row r: [row_ptr[r], row_ptr[r+1])
+    int max_col_upto[kMaxRows + 1] = {}; // largest column referenced by rows < r
+    int max_deg_upto[kMaxRows + 1] = {}; // largest row degree among rows < r
+    uint32_t *d_edges = nullptr;         // device [E_total]: (column << 16) | (shift mod Z)
+    int *d_row_ptr = nullptr;            // device [M_bg + 1]
+    int *d_status = nullptr;             // device status word (ldpc_status of the first error)
+    int device = 0;
+    // staging buffers of ldpc_decode_host (guarded by host_mu)
+    std::mutex host_mu;
+    void *d_stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+// Everything a decode kernel needs, passed by value.
+struct DecodeParams {
+    const uint32_t *edges;    // [E]
+    const int *row_ptr;       // [n_rows + 1]
+    int n_rows, E, Z, n_cols, K_b;
+    int punct, n_tx, max_iter, early_stop, batch;
+    int algo;
+    float alpha, offset;
+    int offset_q;
+    const float *learned;     // [max_iter][n_rows][2] or null
+    const void *llr;          // [batch][n_tx]
+    uint8_t *bits;            // [batch][ceil(K/8)]
+    int32_t *iters;           // [batch]
+    void *post;               // [batch][n_cols * Z] or null
+    void *c2v;                // [batch][E * Z] or null
+    int *status;              // device status word
+};
+
+// Launch entry for the layered decoder (decode_layered.cu).  Returns LDPC_OK or an error
+// found while configuring the launch.
+ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t stream);
+
+void count_launch();
+
+}  // namespace ldpc

@@ -1,0 +1,70 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every symbol the header declares,
+and host-side argument validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2009_05534_gb300 import build
+    build.build()
+    import paper_2009_05534_gb300 as pkg
+    return pkg.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ldpc_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    import paper_2009_05534_gb300 as pkg
+    decl = _declared()
+    assert decl, "no declarations found"
+    for name in decl:
+        assert hasattr(L, name), name
+    assert set(pkg.ABI_SYMBOLS) <= decl
+
+
+def test_status_strings(L):
+    for k, v in {0: b"LDPC_OK", 1: b"LDPC_ERR_INVALID_ARG", 5: b"LDPC_ERR_TIMEOUT"}.items():
+        assert L.ldpc_status_string(k) == v
+
+
+def test_default_opts(L):
+    import paper_2009_05534_gb300 as pkg
+    o = pkg.DecodeOpts()
+    L.ldpc_decode_opts_default(ctypes.byref(o))
+    assert (o.llr_type, o.algo, o.offset_q, o.punct_cols, o.early_stop, o.cluster_size) == \
+        (pkg.LLR_INT8, pkg.OFFSET, 1, 2, 1, 1)
+    assert abs(o.alpha - 0.75) < 1e-7
+
+
+def test_invalid_args_rejected_on_host(L):
+    import numpy as np
+    h = ctypes.c_void_p()
+    base = np.zeros((4, 8), np.int16)
+    p = base.ctypes.data_as(ctypes.c_void_p)
+    assert L.ldpc_graph_create(None, 4, 8, 2, 16, ctypes.byref(h)) == 1
+    assert L.ldpc_graph_create(p, 0, 8, 2, 16, ctypes.byref(h)) == 1
+    assert L.ldpc_graph_create(p, 4, 8, 8, 16, ctypes.byref(h)) == 1       # K_b >= N_bg
+    assert L.ldpc_graph_create(p, 4, 8, 2, 0, ctypes.byref(h)) == 1
+    assert L.ldpc_graph_create(p, 4, 8, 2, 2048, ctypes.byref(h)) == 1
+    bad = base.copy()
+    bad[0, 0] = -5
+    assert L.ldpc_graph_create(bad.ctypes.data_as(ctypes.c_void_p), 4, 8, 2, 16,
+                               ctypes.byref(h)) == 1
+    assert L.ldpc_graph_create(p, 4, 8, 2, 16, None) == 1
+    assert L.ldpc_decode(None, None, 1, 10, None, None, None, None) == 1
+    assert L.ldpc_graph_edges(None, 0) == -1
+    assert L.ldpc_graph_destroy(None) == 1
