@@ -105,6 +105,11 @@ static int graph_build(const int16_t *base, int M_bg, int N_bg, int K_b, int Z, 
         }
     }
     g->row_ptr[n_rows] = e;
+    for (int r = 0; r < n_rows; ++r)
+        if (g->row_ptr[r + 1] - g->row_ptr[r] < 2) {   /* min over the other edges must exist */
+            graph_free(g);
+            return OR_BAD_ARG;
+        }
     return OR_OK;
 }
 

@@ -262,6 +262,11 @@ ldpc_status launch_t(const DecodeParams &p, cudaStream_t stream) {
 }  // namespace
 
 ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t stream) {
+    int dev = 0, smem_optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (rowpair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
+        return launch_rowpair(p, p.max_deg, stream);
     switch (llr_type) {
     case LDPC_LLR_INT8:
         return launch_t<ArithI8>(p, stream);

@@ -1,0 +1,373 @@
+// Row-pair fp16x2 layered min-sum kernel for 8-bit offset min-sum (sm_103a).
+//
+// Same method as the generic kernel (paper Sec. III layered min-sum with correction,
+// Sec. IV per-row m1 / m2 / sign quantities, a1..a6 of the hot path), mapped for
+// throughput on GB300:
+//
+// * Lanes.  Check rows i and i + H (H = Z/2) of a layer travel together in one 32-bit
+//   register as two binary16 lanes.  The 8-bit LLRs are integers in [-127, 127]; every
+//   intermediate value is an integer of magnitude below 2048, so binary16 holds it
+//   exactly and the results are bit-identical to 8-bit fixed-point arithmetic.
+// * Posteriors in shared memory are stored biased by 1152: a word holds
+//   (L[cZ+j] + 1152, L[cZ+j+H] + 1152) for j < H.  Biased values lie in [1025, 1279],
+//   where binary16 has spacing 1, and the bit pattern of 1024 + b is 0x6400 | b.
+// * Check-to-variable messages are kept expanded, one byte per (edge, row), as c + 128.
+//   One PRMT that inserts the byte under the exponent 0x64 turns it into binary16
+//   c + 1152, so v = (L + 1152) - (c + 1152) needs no further conversion, and the new
+//   message c' + 1152 = fma(|m'|, +-1, 1152) is stored back by taking its low byte.
+// * Circulant gather: row j (< H) of a circulant with shift s = qH + u reads word
+//   (j + u) mod H with its halves exchanged when q xor [j + u >= H]; the same
+//   permutation writes the result back.
+// * Check node: min.xorsign.abs.f16x2 gives min(|m1|, |v|) with the sign product in one
+//   instruction; m2 follows from max.xorsign / min.xorsign.  The new message magnitude
+//   uses  excl = max(m1', (m1 + m2 - offset) - |v|): it equals m2' on the argmin edge and
+//   m1' elsewhere (ties give m2 = m1), so no argmin index is needed on the forward pass.
+// * Two threads share a row pair (edges split even / odd) and merge their partial
+//   m1 / m2 / sign with one shuffle exchange.
+#include "ldpc_internal.h"
+
+namespace ldpc {
+namespace {
+
+constexpr uint32_t kOne2 = 0x3C003C00u;     // (1.0, 1.0)
+constexpr uint32_t kNegOne2 = 0xBC00BC00u;  // (-1.0, -1.0)
+constexpr uint32_t kP127 = 0x57F057F0u;     // 127.0
+constexpr uint32_t kN127 = 0xD7F0D7F0u;     // -127.0
+constexpr uint32_t kBias2 = 0x64806480u;    // 1152.0
+constexpr uint32_t kLbLo = 0x64016401u;     // 1025.0 = -127 + 1152
+constexpr uint32_t kLbHi = 0x64FF64FFu;     // 1279.0 =  127 + 1152
+constexpr uint32_t kInf2 = 0x7C007C00u;
+constexpr uint32_t kSign2 = 0x80008000u;
+constexpr uint32_t kAbs2 = 0x7FFF7FFFu;
+constexpr int kMaxDeg = 20;
+
+__device__ __forceinline__ uint32_t h2sub(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2add(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2fma(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2relu_fma(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2min(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2max(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// min(|a|, |b|) with sign(a) xor sign(b)
+__device__ __forceinline__ uint32_t h2minxs(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2maxxs(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(s));
+    return d;
+}
+// per-lane (a < b) of binary16 values -> 0xFFFF / 0 per lane
+__device__ __forceinline__ uint32_t h2lt_mask(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("set.lt.u32.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Per-edge gather metadata for row pair j of a layer:
+//   word = j + base_nw            if j <  thresh   (no wrap), halves permuted by sel_nw
+//   word = j + base_nw - H        if j >= thresh   (wrap),    halves permuted by sel_w
+struct EdgeMeta {
+    int base_nw;       // c*H + u
+    int thresh;        // H - u
+    uint32_t sel_nw;   // 0x3210 or 0x1032
+    uint32_t sel_w;
+};
+
+struct PairParams {
+    DecodeParams p;
+    int H;
+    int max_deg;
+};
+
+struct Smem {
+    EdgeMeta *meta;      // [E]
+    int *row;            // [n_rows + 1]
+    uint32_t *Lb;        // [n_cols][H] words
+    uint16_t *c2v;       // [E][H] byte pairs
+};
+
+// J = edges handled by the first thread of a pair (ceil(d/2)); the second thread handles
+// floor(d/2), so only its last slot is ever idle.
+template <int J>
+__device__ __forceinline__ void process_row(const Smem &s, int e0, int d, int H, int w, int k,
+                                            bool active) {
+    const int cnt = (d - k + 1) >> 1;
+    uint32_t v[J];
+    int addr[J];
+    uint32_t sel[J];
+    uint32_t m1 = kInf2, m2 = kInf2;
+    if (active) {
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+            if (jj < cnt) {
+                const int e = e0 + k + 2 * jj;
+                const EdgeMeta mt = s.meta[e];
+                const bool wr = w >= mt.thresh;
+                const int a = w + mt.base_nw - (wr ? H : 0);
+                const uint32_t sl = wr ? mt.sel_w : mt.sel_nw;
+                const uint32_t X = prmt(s.Lb[a], 0u, sl);
+                const uint32_t M = prmt((uint32_t)s.c2v[e * H + w], 0x64646464u, 0x4140u);
+                uint32_t x = h2sub(X, M);
+                x = h2max(h2min(x, kP127), kN127);
+                const uint32_t hi = h2maxxs(m1, x);
+                m2 = h2minxs(m2, hi);
+                m1 = h2minxs(m1, x);
+                v[jj] = x;
+                addr[jj] = a;
+                sel[jj] = sl;
+            }
+        }
+    }
+    // merge the partner thread's partial reduction (edges of the other parity)
+    const uint32_t o1 = __shfl_xor_sync(0xffffffffu, m1, 1);
+    const uint32_t o2 = __shfl_xor_sync(0xffffffffu, m2, 1);
+    {
+        const uint32_t hi = h2maxxs(m1, o1);
+        m2 = h2minxs(h2minxs(m2, o2), hi);
+        m1 = h2minxs(m1, o1);
+    }
+    if (!active) return;
+    const uint32_t SO = (m1 & kSign2) | kOne2;          // +-1.0: sign product S per lane
+    const uint32_t a1 = m1 & kAbs2, a2 = m2 & kAbs2;
+    const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);   // max(m1 - 1, 0)
+    const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);      // m1 + m2 - 1
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+        if (jj < cnt) {
+            const int e = e0 + k + 2 * jj;
+            const uint32_t x = v[jj];
+            const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
+            const uint32_t sg = (x & kSign2) ^ SO;            // S xor sgn(x), as +-1.0
+            const uint32_t Cm = h2fma(ex, sg, kBias2);        // c' + 1152
+            uint32_t Lb = h2add(Cm, x);                       // (x + c') + 1152
+            Lb = h2max(h2min(Lb, kLbHi), kLbLo);
+            s.Lb[addr[jj]] = prmt(Lb, 0u, sel[jj]);
+            s.c2v[e * H + w] = (uint16_t)prmt(Cm, 0u, 0x3320u);
+        }
+    }
+}
+
+// Specialised for up to 5 edges per thread (row degree <= 10); rows of degree 11..20 use
+// the 10-slot body with the unused slots predicated off.  Fewer instantiations keep the
+// register allocation of the whole kernel below the spill point.
+__device__ __forceinline__ void dispatch_row(int d, const Smem &s, int e0, int H, int w, int k,
+                                             bool active) {
+    switch ((d + 1) >> 1) {
+    case 1: process_row<1>(s, e0, d, H, w, k, active); break;
+    case 2: process_row<2>(s, e0, d, H, w, k, active); break;
+    case 3: process_row<3>(s, e0, d, H, w, k, active); break;
+    case 4: process_row<4>(s, e0, d, H, w, k, active); break;
+    case 5: process_row<5>(s, e0, d, H, w, k, active); break;
+    default: process_row<10>(s, e0, d, H, w, k, active); break;
+    }
+}
+
+// parity of the hard decisions (L < 0  <=>  biased value < 1152) of my edges of a row pair
+__device__ __forceinline__ uint32_t row_parity(const Smem &s, int e0, int d, int H, int w,
+                                               int k) {
+    uint32_t par = 0;
+    for (int j = k; j < d; j += 2) {
+        const EdgeMeta mt = s.meta[e0 + j];
+        const bool wr = w >= mt.thresh;
+        const int a = w + mt.base_nw - (wr ? H : 0);
+        const uint32_t X = prmt(s.Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw);
+        par ^= h2lt_mask(X, kBias2);
+    }
+    return par;
+}
+
+__global__ void __launch_bounds__(384, 1) rowpair_kernel(PairParams pp) {
+    const DecodeParams &p = pp.p;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
+    Smem s;
+    s.meta = reinterpret_cast<EdgeMeta *>(smem);
+    s.row = reinterpret_cast<int *>(s.meta + E);
+    size_t off = (size_t)E * sizeof(EdgeMeta) + (size_t)(n_rows + 1) * 4;
+    off = (off + 15) & ~(size_t)15;
+    s.Lb = reinterpret_cast<uint32_t *>(smem + off);
+    off += (size_t)n_cols * H * 4;
+    s.c2v = reinterpret_cast<uint16_t *>(smem + off);
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int e = tid; e < E; e += nthr) {
+        const uint32_t ed = p.edges[e];
+        const int c = (int)(ed >> 16), sh = (int)(ed & 0xffffu);
+        const int q = sh >= H ? 1 : 0, u = sh - q * H;
+        EdgeMeta m;
+        m.base_nw = c * H + u;
+        m.thresh = H - u;
+        m.sel_nw = q ? 0x1032u : 0x3210u;
+        m.sel_w = q ? 0x3210u : 0x1032u;
+        s.meta[e] = m;
+    }
+    for (int r = tid; r <= n_rows; r += nthr) s.row[r] = p.row_ptr[r];
+
+    const int w = tid >> 1, k = tid & 1;
+    const bool active = w < H;
+    const int K = p.K_b * Z;
+    const int nbytes = (K + 7) >> 3;
+    const int lo = p.punct * Z;
+    const int8_t *llr_all = reinterpret_cast<const int8_t *>(p.llr);
+
+    for (int cw = blockIdx.x; cw < p.batch; cw += gridDim.x) {
+        // a0: biased posteriors from the channel LLRs; messages zero (stored as 0x80)
+        const int8_t *llr = llr_all + (size_t)cw * p.n_tx;
+        for (int c = 0; c < n_cols; ++c) {
+            for (int j = tid; j < H; j += nthr) {
+                const int t0 = c * Z + j - lo, t1 = t0 + H;
+                const uint32_t b0 = (t0 >= 0 && t0 < p.n_tx) ? (uint8_t)llr[t0] : 0u;
+                const uint32_t b1 = (t1 >= 0 && t1 < p.n_tx) ? (uint8_t)llr[t1] : 0u;
+                s.Lb[c * H + j] = 0x64006400u | ((b0 ^ 0x80u) | ((b1 ^ 0x80u) << 16));
+            }
+        }
+        {
+            uint32_t *c2 = reinterpret_cast<uint32_t *>(s.c2v);
+            const int nw = (E * H) >> 1;
+            for (int i = tid; i < nw; i += nthr) c2[i] = 0x80808080u;
+            if ((E * H) & 1)
+                if (tid == 0) s.c2v[E * H - 1] = 0x8080u;
+        }
+        __syncthreads();
+
+        int done = p.max_iter;
+#pragma unroll 1
+        for (int t = 1; t <= p.max_iter; ++t) {
+#pragma unroll 1
+            for (int r = 0; r < n_rows; ++r) {
+                const int e0 = s.row[r], d = s.row[r + 1] - e0;
+                dispatch_row(d, s, e0, H, w, k, active);
+                __syncthreads();
+            }
+            if (p.early_stop) {
+                int bad = 0;
+                for (int r = 0; r < n_rows; ++r) {
+                    const int e0 = s.row[r], d = s.row[r + 1] - e0;
+                    uint32_t par = active ? row_parity(s, e0, d, H, w, k) : 0u;
+                    par ^= __shfl_xor_sync(0xffffffffu, par, 1);
+                    bad = __any_sync(0xffffffffu, par != 0u);
+                    if (bad) break;
+                }
+                if (__syncthreads_or(bad) == 0) {
+                    done = t;
+                    break;
+                }
+            }
+        }
+
+        // a6: hard bits of the K information bits, LSB first
+        for (int b = tid; b < nbytes; b += nthr) {
+            unsigned x = 0;
+            for (int kk = 0; kk < 8; ++kk) {
+                const int j = 8 * b + kk;
+                if (j >= K) break;
+                const int c = j / Z, i = j - c * Z;
+                const int lane = i >= H ? 1 : 0;
+                const uint32_t wd = s.Lb[c * H + i - lane * H];
+                const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                if (h < 0x6480u) x |= 1u << kk;
+            }
+            p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
+        }
+        if (tid == 0) p.iters[cw] = done;
+        if (p.post) {
+            int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw * n_cols * Z;
+            for (int c = 0; c < n_cols; ++c)
+                for (int i = tid; i < Z; i += nthr) {
+                    const int lane = i >= H ? 1 : 0;
+                    const uint32_t wd = s.Lb[c * H + i - lane * H];
+                    const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                    po[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
+                }
+        }
+        if (p.c2v) {
+            int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * E * Z;
+            for (int e = 0; e < E; ++e)
+                for (int i = tid; i < Z; i += nthr) {
+                    const int lane = i >= H ? 1 : 0;
+                    const uint32_t pr = s.c2v[e * H + i - lane * H];
+                    const uint32_t b = lane ? (pr >> 8) : (pr & 0xffu);
+                    co[e * Z + i] = (int8_t)(uint8_t)((b & 0xffu) ^ 0x80u);
+                }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t rowpair_smem_bytes(int E, int n_rows, int n_cols, int Z) {
+    const int H = Z / 2;
+    size_t off = (size_t)E * sizeof(EdgeMeta) + (size_t)(n_rows + 1) * 4;
+    off = (off + 15) & ~(size_t)15;
+    off += (size_t)n_cols * H * 4;
+    off += (size_t)E * H * 2;
+    return (off + 15) & ~(size_t)15;
+}
+
+bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin) {
+    if (llr_type != LDPC_LLR_INT8 || p.algo != LDPC_OFFSET || p.offset_q != 1) return false;
+    if ((p.Z & 1) || p.Z < 2 || p.Z > 384 || max_deg > kMaxDeg || max_deg < 2) return false;
+    if ((size_t)p.n_cols * (p.Z / 2) >= (1u << 30)) return false;
+    return rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z) <= smem_optin;
+}
+
+ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream) {
+    PairParams pp;
+    pp.p = p;
+    pp.H = p.Z / 2;
+    pp.max_deg = max_deg;
+    const size_t smem = rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z);
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(rowpair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    int threads = ((2 * pp.H + 31) / 32) * 32;
+    if (threads > 1024) return LDPC_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowpair_kernel, threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return LDPC_ERR_UNSUPPORTED;
+    int grid = n_sm * per_sm;
+    if (grid > p.batch) grid = p.batch;
+    rowpair_kernel<<<grid, threads, smem, stream>>>(pp);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+}  // namespace ldpc

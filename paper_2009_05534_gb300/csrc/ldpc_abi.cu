@@ -73,11 +73,12 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
         delete g;
         return LDPC_ERR_OUT_OF_MEMORY;
     }
-    int e = 0, maxc = -1, maxd = 0;
+    int e = 0, maxc = -1, maxd = 0, mind = 1 << 30;
     for (int r = 0; r < M_bg; ++r) {
         g->row_ptr[r] = e;
         g->max_col_upto[r] = maxc;
         g->max_deg_upto[r] = maxd;
+        g->min_deg_upto[r] = mind;
         int d = 0;
         for (int c = 0; c < N_bg; ++c) {
             const int v = base[r * N_bg + c];
@@ -87,10 +88,12 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
             ++d;
         }
         if (d > maxd) maxd = d;
+        if (d < mind) mind = d;
     }
     g->row_ptr[M_bg] = e;
     g->max_col_upto[M_bg] = maxc;
     g->max_deg_upto[M_bg] = maxd;
+    g->min_deg_upto[M_bg] = mind;
     cudaGetDevice(&g->device);
     ldpc_status st = LDPC_OK;
     if (cudaMalloc(&g->d_edges, sizeof(uint32_t) * E) != cudaSuccess ||
@@ -165,6 +168,8 @@ static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int
     if (n_rows < 1 || n_rows > g->M_bg) return LDPC_ERR_INVALID_ARG;
     const int n_cols = g->K_b + n_rows;
     if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
+    // every used check row needs two edges (a min over the other edges must exist)
+    if (g->min_deg_upto[n_rows] < 2) return LDPC_ERR_UNSUPPORTED;
     if (o.punct_cols < 0 || o.punct_cols > n_cols) return LDPC_ERR_INVALID_ARG;
     const int n_tx = o.n_tx == 0 ? (n_cols - o.punct_cols) * g->Z : o.n_tx;
     if (n_tx < 0 || o.punct_cols * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
@@ -182,6 +187,7 @@ static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int
     p.Z = g->Z;
     p.n_cols = n_cols;
     p.K_b = g->K_b;
+    p.max_deg = g->max_deg_upto[n_rows];
     p.punct = o.punct_cols;
     p.n_tx = n_tx;
     p.max_iter = max_iter;

@@ -21,6 +21,7 @@ struct Graph {
     int row_ptr[kMaxRows + 1] = {};      // edges of row r: [row_ptr[r], row_ptr[r+1])
     int max_col_upto[kMaxRows + 1] = {}; // largest column referenced by rows < r
     int max_deg_upto[kMaxRows + 1] = {}; // largest row degree among rows < r
+    int min_deg_upto[kMaxRows + 1] = {}; // smallest row degree among rows < r
     uint32_t *d_edges = nullptr;         // device [E_total]: (column << 16) | (shift mod Z)
     int *d_row_ptr = nullptr;            // device [M_bg + 1]
     int *d_status = nullptr;             // device status word (ldpc_status of the first error)
@@ -36,6 +37,7 @@ struct DecodeParams {
     const uint32_t *edges;    // [E]
     const int *row_ptr;       // [n_rows + 1]
     int n_rows, E, Z, n_cols, K_b;
+    int max_deg;              // largest row degree among the used rows
     int punct, n_tx, max_iter, early_stop, batch;
     int algo;
     float alpha, offset;
@@ -52,6 +54,10 @@ struct DecodeParams {
 // Launch entry for the layered decoder (decode_layered.cu).  Returns LDPC_OK or an error
 // found while configuring the launch.
 ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t stream);
+
+// Row-pair fp16x2 kernel for 8-bit offset min-sum (decode_rowpair.cu).
+bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
+ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream);
 
 void count_launch();
 

@@ -211,3 +211,29 @@ def test_int8_full_batch_sampled(ldpc):
                                 max_iter=10, early_stop=False, threads=8)
     assert np.array_equal(gb[idx], ref.bits)
     assert (iters == 10).all()
+
+
+def test_int8_custom_table_degrees_11_to_18(ldpc):
+    """A user base table with row degrees 11..18 (the predicated wide-row path)."""
+    rng = np.random.default_rng(7)
+    M, K_b, Z = 6, 24, 32
+    N = K_b + M
+    base = np.full((M, N), -1, np.int16)
+    for r in range(M):
+        d = 11 + r + (r > 3)                  # 11, 12, 13, 14, 16, 17
+        cols = rng.choice(K_b + r, size=d - 1, replace=False)
+        base[r, cols] = rng.integers(0, 384, size=d - 1)
+        base[r, K_b + r] = 0
+    from synth import info_bits
+    B = 12
+    llr = rng.integers(-40, 41, size=(B, (N - 2) * Z)).astype(np.int8)
+    ref = oracle.decode_layered(base, K_b, Z, M, llr, algo=oracle.OFFSET, offset_q=1,
+                                max_iter=4, early_stop=False, want_post=True, want_c2v=True)
+    g = ldpc.Graph(base, K_b, Z)
+    bits, iters, post, c2v = ldpc.decode(g, torch.from_numpy(llr).cuda(), 4, early_stop=False,
+                                         debug=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(post.cpu().numpy(), ref.post)
+    assert np.array_equal(c2v.cpu().numpy(), ref.c2v)
+    assert np.array_equal(ldpc.unpack_bits(bits.cpu().numpy(), K_b * Z), ref.bits)
+    g.close()
