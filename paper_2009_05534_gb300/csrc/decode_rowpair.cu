@@ -41,6 +41,10 @@ constexpr uint32_t kSign2 = 0x80008000u;
 constexpr uint32_t kAbs2 = 0x7FFF7FFFu;
 constexpr int kMaxDeg = 20;
 
+#ifndef LDPC_ROWPAIR_ALPHA
+#define LDPC_ROWPAIR_ALPHA 4   // threads per row pair
+#endif
+
 __device__ __forceinline__ uint32_t h2sub(uint32_t a, uint32_t b) {
     uint32_t d;
     asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
@@ -117,12 +121,12 @@ struct Smem {
     uint16_t *c2v;       // [E][H] byte pairs
 };
 
-// J = edges handled by the first thread of a pair (ceil(d/2)); the second thread handles
-// floor(d/2), so only its last slot is ever idle.
-template <int J>
+// ALPHA threads share a row pair; thread k handles edges k, k + ALPHA, ...  J is the slot
+// count of the first thread (ceil(d / ALPHA)); later threads may leave their last slot idle.
+template <int ALPHA, int J>
 __device__ __forceinline__ void process_row(const Smem &s, int e0, int d, int H, int w, int k,
                                             bool active) {
-    const int cnt = (d - k + 1) >> 1;
+    const int cnt = (d - k + ALPHA - 1) / ALPHA;
     uint32_t v[J];
     int addr[J];
     uint32_t sel[J];
@@ -131,7 +135,7 @@ __device__ __forceinline__ void process_row(const Smem &s, int e0, int d, int H,
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) {
             if (jj < cnt) {
-                const int e = e0 + k + 2 * jj;
+                const int e = e0 + k + ALPHA * jj;
                 const EdgeMeta mt = s.meta[e];
                 const bool wr = w >= mt.thresh;
                 const int a = w + mt.base_nw - (wr ? H : 0);
@@ -149,10 +153,11 @@ __device__ __forceinline__ void process_row(const Smem &s, int e0, int d, int H,
             }
         }
     }
-    // merge the partner thread's partial reduction (edges of the other parity)
-    const uint32_t o1 = __shfl_xor_sync(0xffffffffu, m1, 1);
-    const uint32_t o2 = __shfl_xor_sync(0xffffffffu, m2, 1);
-    {
+    // butterfly merge of the partial reductions of the ALPHA threads (Sec. IV, Fig. 3)
+#pragma unroll
+    for (int sh = 1; sh < ALPHA; sh <<= 1) {
+        const uint32_t o1 = __shfl_xor_sync(0xffffffffu, m1, sh);
+        const uint32_t o2 = __shfl_xor_sync(0xffffffffu, m2, sh);
         const uint32_t hi = h2maxxs(m1, o1);
         m2 = h2minxs(h2minxs(m2, o2), hi);
         m1 = h2minxs(m1, o1);
@@ -165,7 +170,7 @@ __device__ __forceinline__ void process_row(const Smem &s, int e0, int d, int H,
 #pragma unroll
     for (int jj = 0; jj < J; ++jj) {
         if (jj < cnt) {
-            const int e = e0 + k + 2 * jj;
+            const int e = e0 + k + ALPHA * jj;
             const uint32_t x = v[jj];
             const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
             const uint32_t sg = (x & kSign2) ^ SO;            // S xor sgn(x), as +-1.0
@@ -178,26 +183,27 @@ __device__ __forceinline__ void process_row(const Smem &s, int e0, int d, int H,
     }
 }
 
-// Specialised for up to 5 edges per thread (row degree <= 10); rows of degree 11..20 use
-// the 10-slot body with the unused slots predicated off.  Fewer instantiations keep the
-// register allocation of the whole kernel below the spill point.
+// Specialised for up to 5 edges per thread; with ALPHA = 2, rows of degree 11..20 use the
+// 10-slot body with the unused slots predicated off.  Few instantiations keep the register
+// allocation of the whole kernel below the spill point.
+template <int ALPHA>
 __device__ __forceinline__ void dispatch_row(int d, const Smem &s, int e0, int H, int w, int k,
                                              bool active) {
-    switch ((d + 1) >> 1) {
-    case 1: process_row<1>(s, e0, d, H, w, k, active); break;
-    case 2: process_row<2>(s, e0, d, H, w, k, active); break;
-    case 3: process_row<3>(s, e0, d, H, w, k, active); break;
-    case 4: process_row<4>(s, e0, d, H, w, k, active); break;
-    case 5: process_row<5>(s, e0, d, H, w, k, active); break;
-    default: process_row<10>(s, e0, d, H, w, k, active); break;
+    switch ((d + ALPHA - 1) / ALPHA) {
+    case 1: process_row<ALPHA, 1>(s, e0, d, H, w, k, active); break;
+    case 2: process_row<ALPHA, 2>(s, e0, d, H, w, k, active); break;
+    case 3: process_row<ALPHA, 3>(s, e0, d, H, w, k, active); break;
+    case 4: process_row<ALPHA, 4>(s, e0, d, H, w, k, active); break;
+    case 5: process_row<ALPHA, 5>(s, e0, d, H, w, k, active); break;
+    default: process_row<ALPHA, 20 / ALPHA>(s, e0, d, H, w, k, active); break;
     }
 }
 
 // parity of the hard decisions (L < 0  <=>  biased value < 1152) of my edges of a row pair
 __device__ __forceinline__ uint32_t row_parity(const Smem &s, int e0, int d, int H, int w,
-                                               int k) {
+                                               int k, int alpha) {
     uint32_t par = 0;
-    for (int j = k; j < d; j += 2) {
+    for (int j = k; j < d; j += alpha) {
         const EdgeMeta mt = s.meta[e0 + j];
         const bool wr = w >= mt.thresh;
         const int a = w + mt.base_nw - (wr ? H : 0);
@@ -207,7 +213,8 @@ __device__ __forceinline__ uint32_t row_parity(const Smem &s, int e0, int d, int
     return par;
 }
 
-__global__ void __launch_bounds__(384, 1) rowpair_kernel(PairParams pp) {
+template <int ALPHA>
+__global__ void __launch_bounds__(ALPHA * 192, 1) rowpair_kernel(PairParams pp) {
     const DecodeParams &p = pp.p;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(384, 1) rowpair_kernel(PairParams pp) {
     }
     for (int r = tid; r <= n_rows; r += nthr) s.row[r] = p.row_ptr[r];
 
-    const int w = tid >> 1, k = tid & 1;
+    const int w = tid / ALPHA, k = tid % ALPHA;
     const bool active = w < H;
     const int K = p.K_b * Z;
     const int nbytes = (K + 7) >> 3;
@@ -242,22 +249,28 @@ __global__ void __launch_bounds__(384, 1) rowpair_kernel(PairParams pp) {
     const int8_t *llr_all = reinterpret_cast<const int8_t *>(p.llr);
 
     for (int cw = blockIdx.x; cw < p.batch; cw += gridDim.x) {
-        // a0: biased posteriors from the channel LLRs; messages zero (stored as 0x80)
+        // a0: biased posteriors from the channel LLRs (0 -> 1152 for punctured / unsent
+        // bits), messages zero (stored as 0x80)
         const int8_t *llr = llr_all + (size_t)cw * p.n_tx;
-        for (int c = 0; c < n_cols; ++c) {
-            for (int j = tid; j < H; j += nthr) {
-                const int t0 = c * Z + j - lo, t1 = t0 + H;
-                const uint32_t b0 = (t0 >= 0 && t0 < p.n_tx) ? (uint8_t)llr[t0] : 0u;
-                const uint32_t b1 = (t1 >= 0 && t1 < p.n_tx) ? (uint8_t)llr[t1] : 0u;
-                s.Lb[c * H + j] = 0x64006400u | ((b0 ^ 0x80u) | ((b1 ^ 0x80u) << 16));
-            }
-        }
+        for (int i = tid; i < n_cols * H; i += nthr) s.Lb[i] = 0x64806480u;
         {
             uint32_t *c2 = reinterpret_cast<uint32_t *>(s.c2v);
             const int nw = (E * H) >> 1;
             for (int i = tid; i < nw; i += nthr) c2[i] = 0x80808080u;
             if ((E * H) & 1)
                 if (tid == 0) s.c2v[E * H - 1] = 0x8080u;
+        }
+        __syncthreads();
+        {
+            uint16_t *Lh = reinterpret_cast<uint16_t *>(s.Lb);
+#pragma unroll 8
+            for (int t = tid; t < p.n_tx; t += nthr) {
+                const int j = lo + t;
+                const int c = j / Z, i = j - c * Z;
+                const int lane = i >= H ? 1 : 0;
+                Lh[2 * (c * H + i - lane * H) + lane] =
+                    (uint16_t)(0x6400u | ((uint32_t)(uint8_t)llr[t] ^ 0x80u));
+            }
         }
         __syncthreads();
 
@@ -267,15 +280,17 @@ __global__ void __launch_bounds__(384, 1) rowpair_kernel(PairParams pp) {
 #pragma unroll 1
             for (int r = 0; r < n_rows; ++r) {
                 const int e0 = s.row[r], d = s.row[r + 1] - e0;
-                dispatch_row(d, s, e0, H, w, k, active);
+                dispatch_row<ALPHA>(d, s, e0, H, w, k, active);
                 __syncthreads();
             }
             if (p.early_stop) {
                 int bad = 0;
                 for (int r = 0; r < n_rows; ++r) {
                     const int e0 = s.row[r], d = s.row[r + 1] - e0;
-                    uint32_t par = active ? row_parity(s, e0, d, H, w, k) : 0u;
-                    par ^= __shfl_xor_sync(0xffffffffu, par, 1);
+                    uint32_t par = active ? row_parity(s, e0, d, H, w, k, ALPHA) : 0u;
+#pragma unroll
+                    for (int sh = 1; sh < ALPHA; sh <<= 1)
+                        par ^= __shfl_xor_sync(0xffffffffu, par, sh);
                     bad = __any_sync(0xffffffffu, par != 0u);
                     if (bad) break;
                 }
@@ -343,31 +358,37 @@ bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t 
     return rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z) <= smem_optin;
 }
 
+template <int ALPHA>
+static ldpc_status launch_rowpair_t(const PairParams &pp, cudaStream_t stream) {
+    const DecodeParams &p = pp.p;
+    const size_t smem = rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z);
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(rowpair_kernel<ALPHA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    const int threads = ((ALPHA * pp.H + 31) / 32) * 32;
+    if (threads > ALPHA * 192) return LDPC_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowpair_kernel<ALPHA>, threads,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1)
+        return LDPC_ERR_UNSUPPORTED;
+    int grid = n_sm * per_sm;
+    if (grid > p.batch) grid = p.batch;
+    rowpair_kernel<ALPHA><<<grid, threads, smem, stream>>>(pp);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
 ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream) {
     PairParams pp;
     pp.p = p;
     pp.H = p.Z / 2;
     pp.max_deg = max_deg;
-    const size_t smem = rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z);
-    int dev = 0, n_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(rowpair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return LDPC_ERR_CUDA;
-    int threads = ((2 * pp.H + 31) / 32) * 32;
-    if (threads > 1024) return LDPC_ERR_UNSUPPORTED;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowpair_kernel, threads, smem) !=
-            cudaSuccess ||
-        per_sm < 1)
-        return LDPC_ERR_UNSUPPORTED;
-    int grid = n_sm * per_sm;
-    if (grid > p.batch) grid = p.batch;
-    rowpair_kernel<<<grid, threads, smem, stream>>>(pp);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
-    return LDPC_OK;
+    return launch_rowpair_t<LDPC_ROWPAIR_ALPHA>(pp, stream);
 }
 
 }  // namespace ldpc
