@@ -41,9 +41,7 @@ constexpr uint32_t kSign2 = 0x80008000u;
 constexpr uint32_t kAbs2 = 0x7FFF7FFFu;
 constexpr int kMaxDeg = 20;
 
-#ifndef LDPC_ROWPAIR_ALPHA
-#define LDPC_ROWPAIR_ALPHA 4   // threads per row pair
-#endif
+
 
 __device__ __forceinline__ uint32_t h2sub(uint32_t a, uint32_t b) {
     uint32_t d;
@@ -98,7 +96,8 @@ __device__ __forceinline__ uint32_t h2lt_mask(uint32_t a, uint32_t b) {
     return d;
 }
 
-// Per-edge gather metadata for row pair j of a layer:
+// Per-edge gather metadata for row pair j of a layer (kernel parameters, so the warp-uniform
+// edge index turns into constant-bank loads):
 //   word = j + base_nw            if j <  thresh   (no wrap), halves permuted by sel_nw
 //   word = j + base_nw - H        if j >= thresh   (wrap),    halves permuted by sel_w
 struct EdgeMeta {
@@ -108,103 +107,89 @@ struct EdgeMeta {
     uint32_t sel_w;
 };
 
+constexpr int kMaxEdgesP = 1024;
+constexpr int kMaxRowsP = 64;
+
 struct PairParams {
     DecodeParams p;
     int H;
-    int max_deg;
+    int row[kMaxRowsP + 1];
+    EdgeMeta meta[kMaxEdgesP];
 };
 
 struct Smem {
-    EdgeMeta *meta;      // [E]
-    int *row;            // [n_rows + 1]
     uint32_t *Lb;        // [n_cols][H] words
     uint16_t *c2v;       // [E][H] byte pairs
 };
 
-// ALPHA threads share a row pair; thread k handles edges k, k + ALPHA, ...  J is the slot
-// count of the first thread (ceil(d / ALPHA)); later threads may leave their last slot idle.
-template <int ALPHA, int J>
-__device__ __forceinline__ void process_row(const Smem &s, int e0, int d, int H, int w, int k,
-                                            bool active) {
-    const int cnt = (d - k + ALPHA - 1) / ALPHA;
-    uint32_t v[J];
-    int addr[J];
-    uint32_t sel[J];
+// One thread owns row pair w of every layer; D is the row degree (straight-line code).
+template <int D>
+__device__ __forceinline__ void process_row(const PairParams &pp, const Smem &s, int e0, int H,
+                                            int w, bool store) {
+    uint32_t v[D];
+    int addr[D];
+    uint32_t sel[D];
     uint32_t m1 = kInf2, m2 = kInf2;
-    if (active) {
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-            if (jj < cnt) {
-                const int e = e0 + k + ALPHA * jj;
-                const EdgeMeta mt = s.meta[e];
-                const bool wr = w >= mt.thresh;
-                const int a = w + mt.base_nw - (wr ? H : 0);
-                const uint32_t sl = wr ? mt.sel_w : mt.sel_nw;
-                const uint32_t X = prmt(s.Lb[a], 0u, sl);
-                const uint32_t M = prmt((uint32_t)s.c2v[e * H + w], 0x64646464u, 0x4140u);
-                uint32_t x = h2sub(X, M);
-                x = h2max(h2min(x, kP127), kN127);
-                const uint32_t hi = h2maxxs(m1, x);
-                m2 = h2minxs(m2, hi);
-                m1 = h2minxs(m1, x);
-                v[jj] = x;
-                addr[jj] = a;
-                sel[jj] = sl;
-            }
-        }
+    for (int j = 0; j < D; ++j) {
+        const EdgeMeta &mt = pp.meta[e0 + j];
+        const bool wr = w >= mt.thresh;
+        const int a = w + mt.base_nw - (wr ? H : 0);
+        const uint32_t sl = wr ? mt.sel_w : mt.sel_nw;
+        const uint32_t X = prmt(s.Lb[a], 0u, sl);
+        const uint32_t M = prmt((uint32_t)s.c2v[(e0 + j) * H + w], 0x64646464u, 0x4140u);
+        uint32_t x = h2sub(X, M);
+        x = h2max(h2min(x, kP127), kN127);
+        const uint32_t hi = h2maxxs(m1, x);
+        m2 = h2minxs(m2, hi);
+        m1 = h2minxs(m1, x);
+        v[j] = x;
+        addr[j] = a;
+        sel[j] = sl;
     }
-    // butterfly merge of the partial reductions of the ALPHA threads (Sec. IV, Fig. 3)
-#pragma unroll
-    for (int sh = 1; sh < ALPHA; sh <<= 1) {
-        const uint32_t o1 = __shfl_xor_sync(0xffffffffu, m1, sh);
-        const uint32_t o2 = __shfl_xor_sync(0xffffffffu, m2, sh);
-        const uint32_t hi = h2maxxs(m1, o1);
-        m2 = h2minxs(h2minxs(m2, o2), hi);
-        m1 = h2minxs(m1, o1);
-    }
-    if (!active) return;
-    const uint32_t SO = (m1 & kSign2) | kOne2;          // +-1.0: sign product S per lane
+    const uint32_t SO = (m1 & kSign2) | kOne2;               // +-1.0: sign product S per lane
     const uint32_t a1 = m1 & kAbs2, a2 = m2 & kAbs2;
-    const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);   // max(m1 - 1, 0)
-    const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);      // m1 + m2 - 1
+    const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);    // max(m1 - 1, 0)
+    const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);       // m1 + m2 - 1
 #pragma unroll
-    for (int jj = 0; jj < J; ++jj) {
-        if (jj < cnt) {
-            const int e = e0 + k + ALPHA * jj;
-            const uint32_t x = v[jj];
-            const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
-            const uint32_t sg = (x & kSign2) ^ SO;            // S xor sgn(x), as +-1.0
-            const uint32_t Cm = h2fma(ex, sg, kBias2);        // c' + 1152
-            uint32_t Lb = h2add(Cm, x);                       // (x + c') + 1152
-            Lb = h2max(h2min(Lb, kLbHi), kLbLo);
-            s.Lb[addr[jj]] = prmt(Lb, 0u, sel[jj]);
-            s.c2v[e * H + w] = (uint16_t)prmt(Cm, 0u, 0x3320u);
+    for (int j = 0; j < D; ++j) {
+        const uint32_t x = v[j];
+        const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
+        const uint32_t sg = (x & kSign2) ^ SO;                 // S xor sgn(x), as +-1.0
+        const uint32_t Cm = h2fma(ex, sg, kBias2);             // c' + 1152
+        uint32_t Lb = h2add(Cm, x);                            // (x + c') + 1152
+        Lb = h2max(h2min(Lb, kLbHi), kLbLo);
+        if (store) {
+            s.Lb[addr[j]] = prmt(Lb, 0u, sel[j]);
+            s.c2v[(e0 + j) * H + w] = (uint16_t)prmt(Cm, 0u, 0x3320u);
         }
     }
 }
 
-// Specialised for up to 5 edges per thread; with ALPHA = 2, rows of degree 11..20 use the
-// 10-slot body with the unused slots predicated off.  Few instantiations keep the register
-// allocation of the whole kernel below the spill point.
-template <int ALPHA>
-__device__ __forceinline__ void dispatch_row(int d, const Smem &s, int e0, int H, int w, int k,
-                                             bool active) {
-    switch ((d + ALPHA - 1) / ALPHA) {
-    case 1: process_row<ALPHA, 1>(s, e0, d, H, w, k, active); break;
-    case 2: process_row<ALPHA, 2>(s, e0, d, H, w, k, active); break;
-    case 3: process_row<ALPHA, 3>(s, e0, d, H, w, k, active); break;
-    case 4: process_row<ALPHA, 4>(s, e0, d, H, w, k, active); break;
-    case 5: process_row<ALPHA, 5>(s, e0, d, H, w, k, active); break;
-    default: process_row<ALPHA, 20 / ALPHA>(s, e0, d, H, w, k, active); break;
+__device__ __forceinline__ void dispatch_row(int d, const PairParams &pp, const Smem &s, int e0,
+                                             int H, int w, bool store) {
+    switch (d) {
+#define LDPC_ROW_CASE(D) \
+    case D:              \
+        process_row<D>(pp, s, e0, H, w, store); \
+        break;
+        LDPC_ROW_CASE(2) LDPC_ROW_CASE(3) LDPC_ROW_CASE(4) LDPC_ROW_CASE(5) LDPC_ROW_CASE(6)
+        LDPC_ROW_CASE(7) LDPC_ROW_CASE(8) LDPC_ROW_CASE(9) LDPC_ROW_CASE(10) LDPC_ROW_CASE(11)
+        LDPC_ROW_CASE(12) LDPC_ROW_CASE(13) LDPC_ROW_CASE(14) LDPC_ROW_CASE(15)
+        LDPC_ROW_CASE(16) LDPC_ROW_CASE(17) LDPC_ROW_CASE(18) LDPC_ROW_CASE(19)
+        LDPC_ROW_CASE(20)
+#undef LDPC_ROW_CASE
+    default:
+        break;
     }
 }
 
-// parity of the hard decisions (L < 0  <=>  biased value < 1152) of my edges of a row pair
-__device__ __forceinline__ uint32_t row_parity(const Smem &s, int e0, int d, int H, int w,
-                                               int k, int alpha) {
+// parity of the hard decisions (L < 0  <=>  biased value < 1152) of row pair w
+__device__ __forceinline__ uint32_t row_parity(const PairParams &pp, const Smem &s, int e0,
+                                               int d, int H, int w) {
     uint32_t par = 0;
-    for (int j = k; j < d; j += alpha) {
-        const EdgeMeta mt = s.meta[e0 + j];
+    for (int j = 0; j < d; ++j) {
+        const EdgeMeta &mt = pp.meta[e0 + j];
         const bool wr = w >= mt.thresh;
         const int a = w + mt.base_nw - (wr ? H : 0);
         const uint32_t X = prmt(s.Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw);
@@ -213,36 +198,18 @@ __device__ __forceinline__ uint32_t row_parity(const Smem &s, int e0, int d, int
     return par;
 }
 
-template <int ALPHA>
-__global__ void __launch_bounds__(ALPHA * 192, 1) rowpair_kernel(PairParams pp) {
+__global__ void __launch_bounds__(256, 1) rowpair_kernel(const __grid_constant__ PairParams pp) {
     const DecodeParams &p = pp.p;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
     Smem s;
-    s.meta = reinterpret_cast<EdgeMeta *>(smem);
-    s.row = reinterpret_cast<int *>(s.meta + E);
-    size_t off = (size_t)E * sizeof(EdgeMeta) + (size_t)(n_rows + 1) * 4;
-    off = (off + 15) & ~(size_t)15;
-    s.Lb = reinterpret_cast<uint32_t *>(smem + off);
-    off += (size_t)n_cols * H * 4;
-    s.c2v = reinterpret_cast<uint16_t *>(smem + off);
+    s.Lb = reinterpret_cast<uint32_t *>(smem);
+    s.c2v = reinterpret_cast<uint16_t *>(smem + (size_t)n_cols * H * 4);
 
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int e = tid; e < E; e += nthr) {
-        const uint32_t ed = p.edges[e];
-        const int c = (int)(ed >> 16), sh = (int)(ed & 0xffffu);
-        const int q = sh >= H ? 1 : 0, u = sh - q * H;
-        EdgeMeta m;
-        m.base_nw = c * H + u;
-        m.thresh = H - u;
-        m.sel_nw = q ? 0x1032u : 0x3210u;
-        m.sel_w = q ? 0x3210u : 0x1032u;
-        s.meta[e] = m;
-    }
-    for (int r = tid; r <= n_rows; r += nthr) s.row[r] = p.row_ptr[r];
-
-    const int w = tid / ALPHA, k = tid % ALPHA;
-    const bool active = w < H;
+    // threads past the last row pair repeat its work and store nothing
+    const bool store = tid < H;
+    const int w = store ? tid : H - 1;
     const int K = p.K_b * Z;
     const int nbytes = (K + 7) >> 3;
     const int lo = p.punct * Z;
@@ -279,18 +246,15 @@ __global__ void __launch_bounds__(ALPHA * 192, 1) rowpair_kernel(PairParams pp) 
         for (int t = 1; t <= p.max_iter; ++t) {
 #pragma unroll 1
             for (int r = 0; r < n_rows; ++r) {
-                const int e0 = s.row[r], d = s.row[r + 1] - e0;
-                dispatch_row<ALPHA>(d, s, e0, H, w, k, active);
+                const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
+                dispatch_row(d, pp, s, e0, H, w, store);
                 __syncthreads();
             }
             if (p.early_stop) {
                 int bad = 0;
                 for (int r = 0; r < n_rows; ++r) {
-                    const int e0 = s.row[r], d = s.row[r + 1] - e0;
-                    uint32_t par = active ? row_parity(s, e0, d, H, w, k, ALPHA) : 0u;
-#pragma unroll
-                    for (int sh = 1; sh < ALPHA; sh <<= 1)
-                        par ^= __shfl_xor_sync(0xffffffffu, par, sh);
+                    const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
+                    const uint32_t par = row_parity(pp, s, e0, d, H, w);
                     bad = __any_sync(0xffffffffu, par != 0u);
                     if (bad) break;
                 }
@@ -343,52 +307,56 @@ __global__ void __launch_bounds__(ALPHA * 192, 1) rowpair_kernel(PairParams pp) 
 }  // namespace
 
 size_t rowpair_smem_bytes(int E, int n_rows, int n_cols, int Z) {
+    (void)n_rows;
     const int H = Z / 2;
-    size_t off = (size_t)E * sizeof(EdgeMeta) + (size_t)(n_rows + 1) * 4;
-    off = (off + 15) & ~(size_t)15;
-    off += (size_t)n_cols * H * 4;
-    off += (size_t)E * H * 2;
+    size_t off = (size_t)n_cols * H * 4 + (size_t)E * H * 2;
     return (off + 15) & ~(size_t)15;
 }
 
 bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin) {
     if (llr_type != LDPC_LLR_INT8 || p.algo != LDPC_OFFSET || p.offset_q != 1) return false;
-    if ((p.Z & 1) || p.Z < 2 || p.Z > 384 || max_deg > kMaxDeg || max_deg < 2) return false;
-    if ((size_t)p.n_cols * (p.Z / 2) >= (1u << 30)) return false;
+    if ((p.Z & 1) || p.Z < 2 || p.Z > 512 || max_deg > kMaxDeg || max_deg < 2) return false;
+    if (p.E > kMaxEdgesP || p.n_rows > kMaxRowsP) return false;
     return rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z) <= smem_optin;
 }
 
-template <int ALPHA>
-static ldpc_status launch_rowpair_t(const PairParams &pp, cudaStream_t stream) {
-    const DecodeParams &p = pp.p;
+ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream) {
+    (void)max_deg;
+    static thread_local PairParams pp;     // ~17 kB: kept off the stack
+    pp.p = p;
+    const int H = p.Z / 2;
+    pp.H = H;
+    // graph tables travel as kernel parameters (row pointers, per-edge gather metadata)
+    for (int r = 0; r <= p.n_rows; ++r) pp.row[r] = p.h_row_ptr[r];
+    for (int e = 0; e < p.E; ++e) {
+        const uint32_t ed = p.h_edges[e];
+        const int c = (int)(ed >> 16), sh = (int)(ed & 0xffffu);
+        const int q = sh >= H ? 1 : 0, u = sh - q * H;
+        pp.meta[e].base_nw = c * H + u;
+        pp.meta[e].thresh = H - u;
+        pp.meta[e].sel_nw = q ? 0x1032u : 0x3210u;
+        pp.meta[e].sel_w = q ? 0x3210u : 0x1032u;
+    }
     const size_t smem = rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z);
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(rowpair_kernel<ALPHA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(rowpair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
-    const int threads = ((ALPHA * pp.H + 31) / 32) * 32;
-    if (threads > ALPHA * 192) return LDPC_ERR_UNSUPPORTED;
+    const int threads = ((H + 31) / 32) * 32;
+    if (threads > 256) return LDPC_ERR_UNSUPPORTED;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowpair_kernel<ALPHA>, threads,
-                                                      smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowpair_kernel, threads, smem) !=
+            cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;
     int grid = n_sm * per_sm;
     if (grid > p.batch) grid = p.batch;
-    rowpair_kernel<ALPHA><<<grid, threads, smem, stream>>>(pp);
+    rowpair_kernel<<<grid, threads, smem, stream>>>(pp);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
     return LDPC_OK;
-}
-
-ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream) {
-    PairParams pp;
-    pp.p = p;
-    pp.H = p.Z / 2;
-    pp.max_deg = max_deg;
-    return launch_rowpair_t<LDPC_ROWPAIR_ALPHA>(pp, stream);
 }
 
 }  // namespace ldpc

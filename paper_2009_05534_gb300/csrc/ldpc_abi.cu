@@ -68,11 +68,7 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
     g->K_b = K_b;
     g->Z = Z;
     g->E_total = E;
-    uint32_t *h_edges = (uint32_t *)std::malloc(sizeof(uint32_t) * E);
-    if (!h_edges) {
-        delete g;
-        return LDPC_ERR_OUT_OF_MEMORY;
-    }
+    uint32_t *h_edges = g->h_edges;
     int e = 0, maxc = -1, maxd = 0, mind = 1 << 30;
     for (int r = 0; r < M_bg; ++r) {
         g->row_ptr[r] = e;
@@ -107,7 +103,6 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
                cudaMemset(g->d_status, 0, sizeof(int)) != cudaSuccess) {
         st = LDPC_ERR_CUDA;
     }
-    std::free(h_edges);
     if (st != LDPC_OK) {
         cudaGetLastError();
         cudaFree(g->d_edges);
@@ -182,6 +177,8 @@ static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int
     ldpc::DecodeParams p;
     p.edges = g->d_edges;
     p.row_ptr = g->d_row_ptr;
+    p.h_edges = g->h_edges;
+    p.h_row_ptr = g->row_ptr;
     p.n_rows = n_rows;
     p.E = g->row_ptr[n_rows];
     p.Z = g->Z;

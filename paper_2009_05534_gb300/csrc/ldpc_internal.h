@@ -13,6 +13,7 @@ constexpr int kMaxRows = 64;
 constexpr int kMaxCols = 128;
 constexpr int kMaxZ = 1024;
 constexpr int kMaxIter = 64;
+constexpr int kMaxEdges = kMaxRows * kMaxCols;
 
 // Host-side graph object behind ldpc_graph_t.
 struct Graph {
@@ -22,7 +23,8 @@ struct Graph {
     int max_col_upto[kMaxRows + 1] = {}; // largest column referenced by rows < r
     int max_deg_upto[kMaxRows + 1] = {}; // largest row degree among rows < r
     int min_deg_upto[kMaxRows + 1] = {}; // smallest row degree among rows < r
-    uint32_t *d_edges = nullptr;         // device [E_total]: (column << 16) | (shift mod Z)
+    uint32_t h_edges[kMaxEdges] = {};    // (column << 16) | (shift mod Z), row by row
+    uint32_t *d_edges = nullptr;         // device copy of h_edges
     int *d_row_ptr = nullptr;            // device [M_bg + 1]
     int *d_status = nullptr;             // device status word (ldpc_status of the first error)
     int device = 0;
@@ -34,8 +36,10 @@ struct Graph {
 
 // Everything a decode kernel needs, passed by value.
 struct DecodeParams {
-    const uint32_t *edges;    // [E]
-    const int *row_ptr;       // [n_rows + 1]
+    const uint32_t *edges;    // device [E]
+    const int *row_ptr;       // device [n_rows + 1]
+    const uint32_t *h_edges;  // host copies of the same tables
+    const int *h_row_ptr;
     int n_rows, E, Z, n_cols, K_b;
     int max_deg;              // largest row degree among the used rows
     int punct, n_tx, max_iter, early_stop, batch;
