@@ -265,6 +265,8 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
     int dev = 0, smem_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (tmem_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
+        return launch_tmem(p, stream);
     if (rowpair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
         return launch_rowpair(p, p.max_deg, stream);
     switch (llr_type) {

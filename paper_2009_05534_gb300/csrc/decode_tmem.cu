@@ -1,0 +1,433 @@
+// Layered min-sum, 8-bit offset variant, with the check-to-variable messages held in
+// Tensor Memory (sm_103a).  Paper: Sec. III (layered min-sum with correction, stopping
+// rule), Sec. IV (per-row m1 / m2 / sign quantities); hot-path steps a0..a6.
+//
+// Why TMEM.  A BG1-shaped codeword at Z = 384 needs 52 kB of posteriors (shared by all
+// check rows through the circulant gather) and 124 kB of messages that only their own
+// check row ever reads.  Shared memory can hold one codeword, which leaves one codeword's
+// serial chain of 460 layer barriers per SM and a latency-bound SM.  The messages are
+// private per row, so they go to Tensor Memory instead: tcgen05.ld / tcgen05.st of shape
+// 32x32b give every thread its own TMEM lane with warp-uniform, run-time column indices.
+// The 256 kB of TMEM hold the messages of two codewords; shared memory holds their two
+// posterior arrays.  A thread block decodes two codewords at once, each with its own
+// named barrier, so one codeword's barrier and load latency overlaps the other's work.
+//
+// Mapping (per codeword half of the block): thread w owns check rows w and w + H
+// (H = Z/2) of every layer, carried as two binary16 lanes (exact for 8-bit values); the
+// posterior words, bias-by-1152 representation, circulant gather with half swap, and
+// xorsign min-sum are those described in decode_rowpair.cu.  Messages are stored as
+// bytes c + 128, two edges per 32-bit TMEM column (edge j of a row at column
+// tcol[row] + j/2, byte pair j%2), so a row's messages arrive with one or two
+// tcgen05.ld per thread and leave with one or two tcgen05.st.
+#include "f16x2.h"
+#include "ldpc_internal.h"
+
+namespace ldpc {
+namespace {
+
+using namespace h2;
+
+struct EdgeMetaT {
+    int base_nw;       // c*H + u
+    int thresh;        // H - u
+    uint32_t sel_nw;   // 0x3210 or 0x1032
+    uint32_t sel_w;
+};
+
+constexpr int kMaxEdgesT = 1024;
+constexpr int kMaxRowsT = 64;
+constexpr int kTmemCols = 512;
+
+struct TmemParams {
+    DecodeParams p;
+    int H;
+    int wpc;                     // warps per codeword half
+    int ncols;                   // TMEM columns per thread
+    int row[kMaxRowsT + 1];      // edge offsets of the rows
+    int tcol[kMaxRowsT + 1];     // TMEM column offset of each row: sum of ceil(d/2)
+    EdgeMetaT meta[kMaxEdgesT];
+};
+
+// ------------------------------------------------------------------- TMEM access helpers
+
+template <int N>
+__device__ __forceinline__ void tld(uint32_t taddr, uint32_t *r);
+template <>
+__device__ __forceinline__ void tld<1>(uint32_t a, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[0]) : "r"(a));
+}
+template <>
+__device__ __forceinline__ void tld<2>(uint32_t a, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+template <>
+__device__ __forceinline__ void tld<4>(uint32_t a, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+template <>
+__device__ __forceinline__ void tld<8>(uint32_t a, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(a));
+}
+template <int N>
+__device__ __forceinline__ void tst(uint32_t taddr, const uint32_t *r);
+template <>
+__device__ __forceinline__ void tst<1>(uint32_t a, const uint32_t *r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(a), "r"(r[0]));
+}
+template <>
+__device__ __forceinline__ void tst<2>(uint32_t a, const uint32_t *r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(a), "r"(r[0]),
+                 "r"(r[1]));
+}
+template <>
+__device__ __forceinline__ void tst<4>(uint32_t a, const uint32_t *r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]));
+}
+template <>
+__device__ __forceinline__ void tst<8>(uint32_t a, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(a),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]));
+}
+__device__ __forceinline__ void twait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void twait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// load / store N consecutive columns as power-of-two pieces (N <= 15)
+template <int N>
+__device__ __forceinline__ void tload(uint32_t a, uint32_t *r) {
+    if constexpr (N >= 8) {
+        tld<8>(a, r);
+        tload<N - 8>(a + 8, r + 8);
+    } else if constexpr (N >= 4) {
+        tld<4>(a, r);
+        tload<N - 4>(a + 4, r + 4);
+    } else if constexpr (N >= 2) {
+        tld<2>(a, r);
+        tload<N - 2>(a + 2, r + 2);
+    } else if constexpr (N == 1) {
+        tld<1>(a, r);
+    }
+}
+template <int N>
+__device__ __forceinline__ void tstore(uint32_t a, const uint32_t *r) {
+    if constexpr (N >= 8) {
+        tst<8>(a, r);
+        tstore<N - 8>(a + 8, r + 8);
+    } else if constexpr (N >= 4) {
+        tst<4>(a, r);
+        tstore<N - 4>(a + 4, r + 4);
+    } else if constexpr (N >= 2) {
+        tst<2>(a, r);
+        tstore<N - 2>(a + 2, r + 2);
+    } else if constexpr (N == 1) {
+        tst<1>(a, r);
+    }
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ int named_or(int id, int nthreads, int pred) {
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+        " selp.s32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"(pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r;
+}
+
+// --------------------------------------------------------------------------- one layer
+
+// Thread w of a codeword half processes row pair w of a layer of degree D.
+template <int D>
+__device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint32_t tcolumn,
+                                       int e0, int H, int w, bool store) {
+    constexpr int NC = (D + 1) / 2;
+    uint32_t cm[NC];
+    twait_st();                       // this thread's earlier stores to these columns
+    tload<NC>(tcolumn, cm);
+    uint32_t X[D];
+    int addr[D];
+    uint32_t sel[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const EdgeMetaT &mt = pp.meta[e0 + j];
+        const bool wr = w >= mt.thresh;
+        addr[j] = w + mt.base_nw - (wr ? H : 0);
+        sel[j] = wr ? mt.sel_w : mt.sel_nw;
+        X[j] = prmt(Lb[addr[j]], 0u, sel[j]);
+    }
+    twait_ld();
+    uint32_t m1 = kInf2, m2 = kInf2;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        // message byte pair -> binary16 (c + 1152) under the exponent byte 0x64
+        const uint32_t M = prmt(cm[j >> 1], 0x64646464u, (j & 1) ? 0x4342u : 0x4140u);
+        uint32_t x = h2sub(X[j], M);
+        x = h2max(h2min(x, kP127), kN127);
+        const uint32_t hi = h2maxxs(m1, x);
+        m2 = h2minxs(m2, hi);
+        m1 = h2minxs(m1, x);
+        X[j] = x;
+    }
+    const uint32_t SO = (m1 & kSign2) | kOne2;               // +-1.0: sign product per lane
+    const uint32_t a1 = m1 & kAbs2, a2 = m2 & kAbs2;
+    const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);    // max(m1 - 1, 0)
+    const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);       // m1 + m2 - 1
+    uint32_t Cprev = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const uint32_t x = X[j];
+        const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
+        const uint32_t sg = (x & kSign2) ^ SO;                 // S xor sgn(x), as +-1.0
+        const uint32_t Cm = h2fma(ex, sg, kBias2);             // c' + 1152
+        uint32_t L = h2add(Cm, x);                             // (x + c') + 1152
+        L = h2max(h2min(L, kLbHi), kLbLo);
+        if (store) Lb[addr[j]] = prmt(L, 0u, sel[j]);
+        if (j & 1)
+            cm[j >> 1] = prmt(Cprev, Cm, 0x6420u);             // low bytes of both edges
+        else
+            Cprev = Cm;
+    }
+    if (D & 1) cm[NC - 1] = prmt(Cprev, 0u, 0x3320u);
+    tstore<NC>(tcolumn, cm);
+}
+
+__device__ __forceinline__ void tm_dispatch(int d, const TmemParams &pp, uint32_t *Lb,
+                                            uint32_t tcolumn, int e0, int H, int w, bool store) {
+    switch (d) {
+#define LDPC_TM_CASE(D) \
+    case D:             \
+        tm_row<D>(pp, Lb, tcolumn, e0, H, w, store); \
+        break;
+        LDPC_TM_CASE(2) LDPC_TM_CASE(3) LDPC_TM_CASE(4) LDPC_TM_CASE(5) LDPC_TM_CASE(6)
+        LDPC_TM_CASE(7) LDPC_TM_CASE(8) LDPC_TM_CASE(9) LDPC_TM_CASE(10) LDPC_TM_CASE(11)
+        LDPC_TM_CASE(12) LDPC_TM_CASE(13) LDPC_TM_CASE(14) LDPC_TM_CASE(15) LDPC_TM_CASE(16)
+        LDPC_TM_CASE(17) LDPC_TM_CASE(18) LDPC_TM_CASE(19) LDPC_TM_CASE(20)
+#undef LDPC_TM_CASE
+    default:
+        break;
+    }
+}
+
+__device__ __forceinline__ uint32_t tm_parity(const TmemParams &pp, const uint32_t *Lb, int e0,
+                                              int d, int H, int w) {
+    uint32_t par = 0;
+    for (int j = 0; j < d; ++j) {
+        const EdgeMetaT &mt = pp.meta[e0 + j];
+        const bool wr = w >= mt.thresh;
+        const int a = w + mt.base_nw - (wr ? H : 0);
+        par ^= h2lt_mask(prmt(Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kBias2);
+    }
+    return par;
+}
+
+// ---------------------------------------------------------------------------- the kernel
+
+__global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ TmemParams pp) {
+    const DecodeParams &p = pp.p;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tmem_base;
+    const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nthr_half = pp.wpc * 32;
+    const int half = tid / nthr_half;                 // codeword slot of this thread
+    const int ht = tid - half * nthr_half;            // thread index within the half
+    const bool store = ht < H;
+    const int w = store ? ht : H - 1;                 // spare threads shadow the last row pair
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem) + (size_t)half * n_cols * H;
+
+    // TMEM: warp 0 allocates all 512 columns for the block
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&s_tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // this warp's lane quarter and column region
+    const uint32_t tbase = s_tmem_base + ((uint32_t)((warp & 3) * 32) << 16) +
+                           (uint32_t)((warp >> 2) * pp.ncols);
+
+    const int bar_id = 1 + half;
+    const int K = p.K_b * Z;
+    const int nbytes = (K + 7) >> 3;
+    const int lo = p.punct * Z;
+    const int8_t *llr_all = reinterpret_cast<const int8_t *>(p.llr);
+
+    for (int cw = 2 * blockIdx.x + half; cw - half < p.batch; cw += 2 * gridDim.x) {
+        // both halves run the same number of passes; a half without a codeword idles
+        const bool live = cw < p.batch;
+        if (live) {
+            // a0: biased posteriors from the channel LLRs, zero messages
+            const int8_t *llr = llr_all + (size_t)cw * p.n_tx;
+            for (int i = ht; i < n_cols * H; i += nthr_half) Lb[i] = 0x64806480u;
+            {
+                uint32_t z[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) z[k] = 0x80808080u;
+                int c = 0;
+                for (; c + 8 <= pp.ncols; c += 8) tst<8>(tbase + c, z);
+                for (; c < pp.ncols; ++c) tst<1>(tbase + c, z);
+            }
+            named_sync(bar_id, nthr_half);
+            uint16_t *Lh = reinterpret_cast<uint16_t *>(Lb);
+#pragma unroll 8
+            for (int t = ht; t < p.n_tx; t += nthr_half) {
+                const int j = lo + t;
+                const int c = j / Z, i = j - c * Z;
+                const int lane = i >= H ? 1 : 0;
+                Lh[2 * (c * H + i - lane * H) + lane] =
+                    (uint16_t)(0x6400u | ((uint32_t)(uint8_t)llr[t] ^ 0x80u));
+            }
+            named_sync(bar_id, nthr_half);
+
+            int done = p.max_iter;
+#pragma unroll 1
+            for (int t = 1; t <= p.max_iter; ++t) {
+#pragma unroll 1
+                for (int r = 0; r < n_rows; ++r) {
+                    const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
+                    tm_dispatch(d, pp, Lb, tbase + (uint32_t)pp.tcol[r], e0, H, w, store);
+                    named_sync(bar_id, nthr_half);
+                }
+                if (p.early_stop) {
+                    int bad = 0;
+                    for (int r = 0; r < n_rows && !bad; ++r) {
+                        const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
+                        bad = __any_sync(0xffffffffu, tm_parity(pp, Lb, e0, d, H, w) != 0u);
+                    }
+                    if (named_or(bar_id, nthr_half, bad) == 0) {
+                        done = t;
+                        break;
+                    }
+                }
+            }
+
+            // a6: outputs
+            for (int b = ht; b < nbytes; b += nthr_half) {
+                unsigned x = 0;
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int j = 8 * b + kk;
+                    if (j >= K) break;
+                    const int c = j / Z, i = j - c * Z;
+                    const int lane = i >= H ? 1 : 0;
+                    const uint32_t wd = Lb[c * H + i - lane * H];
+                    const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                    if (h < 0x6480u) x |= 1u << kk;
+                }
+                p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
+            }
+            if (ht == 0) p.iters[cw] = done;
+            if (p.post) {
+                int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw * n_cols * Z;
+                for (int c = 0; c < n_cols; ++c)
+                    for (int i = ht; i < Z; i += nthr_half) {
+                        const int lane = i >= H ? 1 : 0;
+                        const uint32_t wd = Lb[c * H + i - lane * H];
+                        const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                        po[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
+                    }
+            }
+            if (p.c2v) {
+                // each thread reads its own TMEM lane: messages of rows w and w + H
+                twait_st();
+                int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * E * Z;
+                for (int r = 0; r < n_rows; ++r) {
+                    const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
+                    for (int j = 0; j < d; ++j) {
+                        uint32_t v;
+                        tld<1>(tbase + (uint32_t)(pp.tcol[r] + (j >> 1)), &v);
+                        twait_ld();
+                        const uint32_t pr = (j & 1) ? (v >> 16) : (v & 0xffffu);
+                        if (store) {
+                            co[(e0 + j) * Z + w] = (int8_t)(uint8_t)((pr & 0xffu) ^ 0x80u);
+                            co[(e0 + j) * Z + w + H] = (int8_t)(uint8_t)(((pr >> 8) & 0xffu) ^ 0x80u);
+                        }
+                    }
+                }
+            }
+        }
+        named_sync(bar_id, nthr_half);
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem_base),
+                     "r"(kTmemCols)
+                     : "memory");
+}
+
+int tmem_columns_per_thread(const DecodeParams &p) {
+    int n = 0;
+    for (int r = 0; r < p.n_rows; ++r) n += (p.h_row_ptr[r + 1] - p.h_row_ptr[r] + 1) / 2;
+    return n;
+}
+
+}  // namespace
+
+bool tmem_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin) {
+    if (llr_type != LDPC_LLR_INT8 || p.algo != LDPC_OFFSET || p.offset_q != 1) return false;
+    if ((p.Z & 1) || p.Z < 2 || p.Z > 384 || max_deg > kMaxDeg || max_deg < 2) return false;
+    if (p.E > kMaxEdgesT || p.n_rows > kMaxRowsT) return false;
+    const int H = p.Z / 2, wpc = (H + 31) / 32;
+    const int depth = (2 * wpc + 3) / 4;
+    if (depth * tmem_columns_per_thread(p) > kTmemCols) return false;
+    return (size_t)2 * p.n_cols * H * 4 <= smem_optin;
+}
+
+ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream) {
+    static thread_local TmemParams pp;     // ~17 kB: kept off the stack
+    pp.p = p;
+    const int H = p.Z / 2;
+    pp.H = H;
+    pp.wpc = (H + 31) / 32;
+    int col = 0;
+    for (int r = 0; r <= p.n_rows; ++r) {
+        pp.row[r] = p.h_row_ptr[r];
+        pp.tcol[r] = col;
+        if (r < p.n_rows) col += (p.h_row_ptr[r + 1] - p.h_row_ptr[r] + 1) / 2;
+    }
+    pp.ncols = col;
+    for (int e = 0; e < p.E; ++e) {
+        const uint32_t ed = p.h_edges[e];
+        const int c = (int)(ed >> 16), sh = (int)(ed & 0xffffu);
+        const int q = sh >= H ? 1 : 0, u = sh - q * H;
+        pp.meta[e].base_nw = c * H + u;
+        pp.meta[e].thresh = H - u;
+        pp.meta[e].sel_nw = q ? 0x1032u : 0x3210u;
+        pp.meta[e].sel_w = q ? 0x3210u : 0x1032u;
+    }
+    // two posterior arrays; at least 120 kB so that a single block occupies the SM (its TMEM
+    // allocation takes all 512 columns)
+    size_t smem = (size_t)2 * p.n_cols * H * 4;
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(tmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    const int threads = 2 * pp.wpc * 32;
+    int grid = (p.batch + 1) / 2;
+    if (grid > n_sm) grid = n_sm;
+    tmem_kernel<<<grid, threads, smem, stream>>>(pp);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+}  // namespace ldpc

@@ -1,0 +1,78 @@
+// binary16x2 helpers shared by the row-pair kernels (values held as 32-bit bit patterns).
+#pragma once
+
+#include <cstdint>
+
+namespace ldpc {
+namespace h2 {
+
+constexpr uint32_t kOne2 = 0x3C003C00u;     // (1.0, 1.0)
+constexpr uint32_t kNegOne2 = 0xBC00BC00u;  // (-1.0, -1.0)
+constexpr uint32_t kP127 = 0x57F057F0u;     // 127.0
+constexpr uint32_t kN127 = 0xD7F0D7F0u;     // -127.0
+constexpr uint32_t kBias2 = 0x64806480u;    // 1152.0
+constexpr uint32_t kLbLo = 0x64016401u;     // 1025.0 = -127 + 1152
+constexpr uint32_t kLbHi = 0x64FF64FFu;     // 1279.0 =  127 + 1152
+constexpr uint32_t kInf2 = 0x7C007C00u;
+constexpr uint32_t kSign2 = 0x80008000u;
+constexpr uint32_t kAbs2 = 0x7FFF7FFFu;
+constexpr int kMaxDeg = 20;
+
+
+
+__device__ __forceinline__ uint32_t h2sub(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2add(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2fma(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2relu_fma(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2min(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2max(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// min(|a|, |b|) with sign(a) xor sign(b)
+__device__ __forceinline__ uint32_t h2minxs(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t h2maxxs(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.xorsign.abs.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(s));
+    return d;
+}
+// per-lane (a < b) of binary16 values -> 0xFFFF / 0 per lane
+__device__ __forceinline__ uint32_t h2lt_mask(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("set.lt.u32.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+
+}  // namespace h2
+}  // namespace ldpc

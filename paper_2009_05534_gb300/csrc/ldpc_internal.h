@@ -59,7 +59,12 @@ struct DecodeParams {
 // found while configuring the launch.
 ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t stream);
 
-// Row-pair fp16x2 kernel for 8-bit offset min-sum (decode_rowpair.cu).
+// Two-codeword row-pair kernel with messages in Tensor Memory (decode_tmem.cu).
+bool tmem_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
+ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream);
+
+// Row-pair fp16x2 kernel for 8-bit offset min-sum, messages in shared memory
+// (decode_rowpair.cu).
 bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream);
 
