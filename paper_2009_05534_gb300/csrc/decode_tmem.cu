@@ -16,9 +16,10 @@
 // (H = Z/2) of every layer, carried as two binary16 lanes (exact for 8-bit values); the
 // posterior words, bias-by-1152 representation, circulant gather with half swap, and
 // xorsign min-sum are those described in decode_rowpair.cu.  Messages are stored as
-// bytes c + 128, two edges per 32-bit TMEM column (edge j of a row at column
-// tcol[row] + j/2, byte pair j%2), so a row's messages arrive with one or two
-// tcgen05.ld per thread and leave with one or two tcgen05.st.
+// bytes c + 128, two edges per 32-bit TMEM column, packed tightly across rows (edge e at
+// column e/2, byte pair e%2), so a row's messages arrive with one or two tcgen05.ld per
+// thread and leave with one or two tcgen05.st; a column shared with the neighbouring row
+// is written back with that row's half unchanged.
 #include "f16x2.h"
 #include "ldpc_internal.h"
 
@@ -42,9 +43,8 @@ struct TmemParams {
     DecodeParams p;
     int H;
     int wpc;                     // warps per codeword half
-    int ncols;                   // TMEM columns per thread
+    int ncols;                   // TMEM columns per thread: ceil(E / 2)
     int row[kMaxRowsT + 1];      // edge offsets of the rows
-    int tcol[kMaxRowsT + 1];     // TMEM column offset of each row: sum of ceil(d/2)
     EdgeMetaT meta[kMaxEdgesT];
 };
 
@@ -146,13 +146,14 @@ __device__ __forceinline__ int named_or(int id, int nthreads, int pred) {
 
 // --------------------------------------------------------------------------- one layer
 
-// Thread w of a codeword half processes row pair w of a layer of degree D.
-template <int D>
+// Thread w of a codeword half processes row pair w of a layer of degree D whose first edge
+// sits in the upper half of its TMEM column when P = 1.
+template <int D, int P>
 __device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint32_t tcolumn,
                                        int e0, int H, int w, bool store) {
-    constexpr int NC = (D + 1) / 2;
+    constexpr int NC = (P + D + 1) / 2;   // columns touched by the row
     uint32_t cm[NC];
-    twait_st();                       // this thread's earlier stores to these columns
+    twait_st();                           // this thread's earlier stores to these columns
     tload<NC>(tcolumn, cm);
     uint32_t X[D];
     int addr[D];
@@ -170,7 +171,8 @@ __device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint3
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         // message byte pair -> binary16 (c + 1152) under the exponent byte 0x64
-        const uint32_t M = prmt(cm[j >> 1], 0x64646464u, (j & 1) ? 0x4342u : 0x4140u);
+        const uint32_t M =
+            prmt(cm[(P + j) >> 1], 0x64646464u, ((P + j) & 1) ? 0x4342u : 0x4140u);
         uint32_t x = h2sub(X[j], M);
         x = h2max(h2min(x, kP127), kN127);
         const uint32_t hi = h2maxxs(m1, x);
@@ -182,31 +184,48 @@ __device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint3
     const uint32_t a1 = m1 & kAbs2, a2 = m2 & kAbs2;
     const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);    // max(m1 - 1, 0)
     const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);       // m1 + m2 - 1
-    uint32_t Cprev = 0;
+    uint32_t C[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const uint32_t x = X[j];
         const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
         const uint32_t sg = (x & kSign2) ^ SO;                 // S xor sgn(x), as +-1.0
-        const uint32_t Cm = h2fma(ex, sg, kBias2);             // c' + 1152
-        uint32_t L = h2add(Cm, x);                             // (x + c') + 1152
+        C[j] = h2fma(ex, sg, kBias2);                          // c' + 1152
+        uint32_t L = h2add(C[j], x);                           // (x + c') + 1152
         L = h2max(h2min(L, kLbHi), kLbLo);
         if (store) Lb[addr[j]] = prmt(L, 0u, sel[j]);
-        if (j & 1)
-            cm[j >> 1] = prmt(Cprev, Cm, 0x6420u);             // low bytes of both edges
-        else
-            Cprev = Cm;
     }
-    if (D & 1) cm[NC - 1] = prmt(Cprev, 0u, 0x3320u);
+    // repack: low bytes of both lanes of each edge; foreign halves of the boundary columns
+    // (neighbouring rows) are kept as loaded
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int jl = 2 * k - P, jh = 2 * k + 1 - P;
+        const int il = jl < 0 ? 0 : jl, ih = jh >= D ? D - 1 : jh;   // in-range indices
+        if (jl >= 0 && jh < D)
+            cm[k] = prmt(C[il], C[ih], 0x6420u);
+        else if (jl >= 0)
+            cm[k] = prmt(C[il], cm[k], 0x7620u);
+        else
+            cm[k] = prmt(cm[k], C[ih], 0x6410u);
+    }
     tstore<NC>(tcolumn, cm);
 }
 
+template <int D>
+__device__ __forceinline__ void tm_row_any(const TmemParams &pp, uint32_t *Lb,
+                                           uint32_t tbase, int e0, int H, int w, bool store) {
+    if (e0 & 1)
+        tm_row<D, 1>(pp, Lb, tbase + (uint32_t)(e0 >> 1), e0, H, w, store);
+    else
+        tm_row<D, 0>(pp, Lb, tbase + (uint32_t)(e0 >> 1), e0, H, w, store);
+}
+
 __device__ __forceinline__ void tm_dispatch(int d, const TmemParams &pp, uint32_t *Lb,
-                                            uint32_t tcolumn, int e0, int H, int w, bool store) {
+                                            uint32_t tbase, int e0, int H, int w, bool store) {
     switch (d) {
 #define LDPC_TM_CASE(D) \
     case D:             \
-        tm_row<D>(pp, Lb, tcolumn, e0, H, w, store); \
+        tm_row_any<D>(pp, Lb, tbase, e0, H, w, store); \
         break;
         LDPC_TM_CASE(2) LDPC_TM_CASE(3) LDPC_TM_CASE(4) LDPC_TM_CASE(5) LDPC_TM_CASE(6)
         LDPC_TM_CASE(7) LDPC_TM_CASE(8) LDPC_TM_CASE(9) LDPC_TM_CASE(10) LDPC_TM_CASE(11)
@@ -299,7 +318,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
 #pragma unroll 1
                 for (int r = 0; r < n_rows; ++r) {
                     const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
-                    tm_dispatch(d, pp, Lb, tbase + (uint32_t)pp.tcol[r], e0, H, w, store);
+                    tm_dispatch(d, pp, Lb, tbase, e0, H, w, store);
                     named_sync(bar_id, nthr_half);
                 }
                 if (p.early_stop) {
@@ -344,17 +363,14 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                 // each thread reads its own TMEM lane: messages of rows w and w + H
                 twait_st();
                 int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * E * Z;
-                for (int r = 0; r < n_rows; ++r) {
-                    const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
-                    for (int j = 0; j < d; ++j) {
-                        uint32_t v;
-                        tld<1>(tbase + (uint32_t)(pp.tcol[r] + (j >> 1)), &v);
-                        twait_ld();
-                        const uint32_t pr = (j & 1) ? (v >> 16) : (v & 0xffffu);
-                        if (store) {
-                            co[(e0 + j) * Z + w] = (int8_t)(uint8_t)((pr & 0xffu) ^ 0x80u);
-                            co[(e0 + j) * Z + w + H] = (int8_t)(uint8_t)(((pr >> 8) & 0xffu) ^ 0x80u);
-                        }
+                for (int e = 0; e < E; ++e) {
+                    uint32_t v;
+                    tld<1>(tbase + (uint32_t)(e >> 1), &v);
+                    twait_ld();
+                    const uint32_t pr = (e & 1) ? (v >> 16) : (v & 0xffffu);
+                    if (store) {
+                        co[e * Z + w] = (int8_t)(uint8_t)((pr & 0xffu) ^ 0x80u);
+                        co[e * Z + w + H] = (int8_t)(uint8_t)(((pr >> 8) & 0xffu) ^ 0x80u);
                     }
                 }
             }
@@ -371,11 +387,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                      : "memory");
 }
 
-int tmem_columns_per_thread(const DecodeParams &p) {
-    int n = 0;
-    for (int r = 0; r < p.n_rows; ++r) n += (p.h_row_ptr[r + 1] - p.h_row_ptr[r] + 1) / 2;
-    return n;
-}
+int tmem_columns_per_thread(const DecodeParams &p) { return (p.E + 1) / 2; }
 
 }  // namespace
 
@@ -395,13 +407,8 @@ ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream) {
     const int H = p.Z / 2;
     pp.H = H;
     pp.wpc = (H + 31) / 32;
-    int col = 0;
-    for (int r = 0; r <= p.n_rows; ++r) {
-        pp.row[r] = p.h_row_ptr[r];
-        pp.tcol[r] = col;
-        if (r < p.n_rows) col += (p.h_row_ptr[r + 1] - p.h_row_ptr[r] + 1) / 2;
-    }
-    pp.ncols = col;
+    for (int r = 0; r <= p.n_rows; ++r) pp.row[r] = p.h_row_ptr[r];
+    pp.ncols = tmem_columns_per_thread(p);
     for (int e = 0; e < p.E; ++e) {
         const uint32_t ed = p.h_edges[e];
         const int c = (int)(ed >> 16), sh = (int)(ed & 0xffffu);

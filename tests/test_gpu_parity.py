@@ -237,3 +237,30 @@ def test_int8_custom_table_degrees_11_to_18(ldpc):
     assert np.array_equal(c2v.cpu().numpy(), ref.c2v)
     assert np.array_equal(ldpc.unpack_bits(bits.cpu().numpy(), K_b * Z), ref.bits)
     g.close()
+
+
+def test_int8_dense_bg1_table_z384(ldpc):
+    """A 46 x 68 table with more edges than fit the Tensor-Memory message store (E > 340
+    at Z = 384), which takes the shared-memory row-pair kernel."""
+    rng = np.random.default_rng(11)
+    M, K_b, Z = 46, 22, 384
+    N = K_b + M
+    base = np.full((M, N), -1, np.int16)
+    for r in range(M):
+        d = int(rng.integers(8, 13))
+        cols = rng.choice(K_b + 4, size=d - 1, replace=False)
+        base[r, cols] = rng.integers(0, 384, size=d - 1)
+        base[r, K_b + r] = 0
+    assert (base >= 0).sum() > 340
+    B = 6
+    llr = rng.integers(-30, 31, size=(B, (N - 2) * Z)).astype(np.int8)
+    ref = oracle.decode_layered(base, K_b, Z, M, llr, algo=oracle.OFFSET, offset_q=1,
+                                max_iter=3, early_stop=False, want_post=True, want_c2v=True,
+                                threads=6)
+    g = ldpc.Graph(base, K_b, Z)
+    bits, iters, post, c2v = ldpc.decode(g, torch.from_numpy(llr).cuda(), 3, early_stop=False,
+                                         debug=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(post.cpu().numpy(), ref.post)
+    assert np.array_equal(c2v.cpu().numpy(), ref.c2v)
+    g.close()
