@@ -44,6 +44,9 @@ struct TmemParams {
     int H;
     int wpc;                     // warps per codeword half
     int ncols;                   // TMEM columns per thread: ceil(E / 2)
+    int use_tma;                 // channel LLRs staged by 1-D bulk copies
+    int stage_bytes;             // per-half staging buffer (multiple of 16)
+    int off_lb, off_stage;       // shared-memory offsets of the posteriors and the staging
     int row[kMaxRowsT + 1];      // edge offsets of the rows
     EdgeMetaT meta[kMaxEdgesT];
 };
@@ -149,7 +152,7 @@ __device__ __forceinline__ int named_or(int id, int nthreads, int pred) {
 // Thread w of a codeword half processes row pair w of a layer of degree D whose first edge
 // sits in the upper half of its TMEM column when P = 1.
 template <int D, int P>
-__device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint32_t tcolumn,
+__device__ __forceinline__ void tm_row(const EdgeMetaT *meta, uint32_t *Lb, uint32_t tcolumn,
                                        int e0, int H, int w, bool store) {
     constexpr int NC = (P + D + 1) / 2;   // columns touched by the row
     uint32_t cm[NC];
@@ -160,7 +163,7 @@ __device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint3
     uint32_t sel[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const EdgeMetaT &mt = pp.meta[e0 + j];
+        const EdgeMetaT mt = meta[e0 + j];             // one broadcast 16-byte load
         const bool wr = w >= mt.thresh;
         addr[j] = w + mt.base_nw - (wr ? H : 0);
         sel[j] = wr ? mt.sel_w : mt.sel_nw;
@@ -188,7 +191,7 @@ __device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint3
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const uint32_t x = X[j];
-        const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
+        const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
         const uint32_t sg = (x & kSign2) ^ SO;                 // S xor sgn(x), as +-1.0
         C[j] = h2fma(ex, sg, kBias2);                          // c' + 1152
         uint32_t L = h2add(C[j], x);                           // (x + c') + 1152
@@ -212,20 +215,20 @@ __device__ __forceinline__ void tm_row(const TmemParams &pp, uint32_t *Lb, uint3
 }
 
 template <int D>
-__device__ __forceinline__ void tm_row_any(const TmemParams &pp, uint32_t *Lb,
+__device__ __forceinline__ void tm_row_any(const EdgeMetaT *meta, uint32_t *Lb,
                                            uint32_t tbase, int e0, int H, int w, bool store) {
     if (e0 & 1)
-        tm_row<D, 1>(pp, Lb, tbase + (uint32_t)(e0 >> 1), e0, H, w, store);
+        tm_row<D, 1>(meta, Lb, tbase + (uint32_t)(e0 >> 1), e0, H, w, store);
     else
-        tm_row<D, 0>(pp, Lb, tbase + (uint32_t)(e0 >> 1), e0, H, w, store);
+        tm_row<D, 0>(meta, Lb, tbase + (uint32_t)(e0 >> 1), e0, H, w, store);
 }
 
-__device__ __forceinline__ void tm_dispatch(int d, const TmemParams &pp, uint32_t *Lb,
+__device__ __forceinline__ void tm_dispatch(int d, const EdgeMetaT *meta, uint32_t *Lb,
                                             uint32_t tbase, int e0, int H, int w, bool store) {
     switch (d) {
 #define LDPC_TM_CASE(D) \
     case D:             \
-        tm_row_any<D>(pp, Lb, tbase, e0, H, w, store); \
+        tm_row_any<D>(meta, Lb, tbase, e0, H, w, store); \
         break;
         LDPC_TM_CASE(2) LDPC_TM_CASE(3) LDPC_TM_CASE(4) LDPC_TM_CASE(5) LDPC_TM_CASE(6)
         LDPC_TM_CASE(7) LDPC_TM_CASE(8) LDPC_TM_CASE(9) LDPC_TM_CASE(10) LDPC_TM_CASE(11)
@@ -237,16 +240,56 @@ __device__ __forceinline__ void tm_dispatch(int d, const TmemParams &pp, uint32_
     }
 }
 
-__device__ __forceinline__ uint32_t tm_parity(const TmemParams &pp, const uint32_t *Lb, int e0,
+__device__ __forceinline__ uint32_t tm_parity(const EdgeMetaT *meta, const uint32_t *Lb, int e0,
                                               int d, int H, int w) {
     uint32_t par = 0;
     for (int j = 0; j < d; ++j) {
-        const EdgeMetaT &mt = pp.meta[e0 + j];
+        const EdgeMetaT mt = meta[e0 + j];
         const bool wr = w >= mt.thresh;
         const int a = w + mt.base_nw - (wr ? H : 0);
         par ^= h2lt_mask(prmt(Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kBias2);
     }
     return par;
+}
+
+// -------------------------------------------------------- channel LLR staging (TMA 1-D)
+
+constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier waits (each try_wait may sleep)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one thread: expect `bytes` and start the bulk copy global -> shared
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    // order the block's earlier generic reads of the buffer before the async-proxy write
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// bounded wait for phase `parity` of the barrier; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------------------- the kernel
@@ -255,6 +298,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
     const DecodeParams &p = pp.p;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tmem_base;
+    __shared__ __align__(8) uint64_t s_bar[2];
     const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nthr_half = pp.wpc * 32;
@@ -262,12 +306,19 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
     const int ht = tid - half * nthr_half;            // thread index within the half
     const bool store = ht < H;
     const int w = store ? ht : H - 1;                 // spare threads shadow the last row pair
-    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem) + (size_t)half * n_cols * H;
+    // shared memory: edge metadata | two posterior arrays | two LLR staging buffers
+    EdgeMetaT *s_meta = reinterpret_cast<EdgeMetaT *>(smem);
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem + pp.off_lb) + (size_t)half * n_cols * H;
+    const int8_t *stage =
+        reinterpret_cast<const int8_t *>(smem + pp.off_stage) + (size_t)half * pp.stage_bytes;
+    uint64_t *bar = &s_bar[half];
 
+    for (int e = tid; e < E; e += blockDim.x) s_meta[e] = pp.meta[e];
+    if (ht == 0 && pp.use_tma) mbar_init(bar);
     // TMEM: warp 0 allocates all 512 columns for the block
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(&s_tmem_base)),
+                         smem_addr(&s_tmem_base)),
                      "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -284,14 +335,18 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
     const int nbytes = (K + 7) >> 3;
     const int lo = p.punct * Z;
     const int8_t *llr_all = reinterpret_cast<const int8_t *>(p.llr);
+    const int stride = 2 * gridDim.x;
+    const int cw0 = 2 * blockIdx.x + half;
+    uint32_t parity = 0;
+    bool failed = false;
+    if (pp.use_tma && ht == 0 && cw0 < p.batch)
+        bulk_load(const_cast<int8_t *>(stage), llr_all + (size_t)cw0 * p.n_tx,
+                  (uint32_t)p.n_tx, bar);
 
-    for (int cw = 2 * blockIdx.x + half; cw - half < p.batch; cw += 2 * gridDim.x) {
+    for (int cw = cw0; cw - half < p.batch; cw += stride) {
         // both halves run the same number of passes; a half without a codeword idles
-        const bool live = cw < p.batch;
-        if (live) {
-            // a0: biased posteriors from the channel LLRs, zero messages
-            const int8_t *llr = llr_all + (size_t)cw * p.n_tx;
-            for (int i = ht; i < n_cols * H; i += nthr_half) Lb[i] = 0x64806480u;
+        if (cw < p.batch && !failed) {
+            // a0: zero messages; biased posteriors from the channel LLRs
             {
                 uint32_t z[8];
 #pragma unroll
@@ -300,83 +355,104 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                 for (; c + 8 <= pp.ncols; c += 8) tst<8>(tbase + c, z);
                 for (; c < pp.ncols; ++c) tst<1>(tbase + c, z);
             }
-            named_sync(bar_id, nthr_half);
-            uint16_t *Lh = reinterpret_cast<uint16_t *>(Lb);
-#pragma unroll 8
-            for (int t = ht; t < p.n_tx; t += nthr_half) {
-                const int j = lo + t;
-                const int c = j / Z, i = j - c * Z;
-                const int lane = i >= H ? 1 : 0;
-                Lh[2 * (c * H + i - lane * H) + lane] =
-                    (uint16_t)(0x6400u | ((uint32_t)(uint8_t)llr[t] ^ 0x80u));
-            }
-            named_sync(bar_id, nthr_half);
-
-            int done = p.max_iter;
-#pragma unroll 1
-            for (int t = 1; t <= p.max_iter; ++t) {
-#pragma unroll 1
-                for (int r = 0; r < n_rows; ++r) {
-                    const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
-                    tm_dispatch(d, pp, Lb, tbase, e0, H, w, store);
-                    named_sync(bar_id, nthr_half);
+            const int8_t *src = llr_all + (size_t)cw * p.n_tx;
+            if (pp.use_tma) {
+                const bool ok = mbar_wait(bar, parity);
+                parity ^= 1u;
+                if (named_or(bar_id, nthr_half, !ok)) {
+                    if (ht == 0) atomicCAS(p.status, 0, (int)LDPC_ERR_TIMEOUT);
+                    failed = true;
                 }
-                if (p.early_stop) {
-                    int bad = 0;
-                    for (int r = 0; r < n_rows && !bad; ++r) {
+                src = stage;
+            }
+            if (!failed) {
+                // word (c, j) holds rows j and j + H of column block c
+                for (int c = 0; c < n_cols; ++c) {
+                    for (int j = ht; j < H; j += nthr_half) {
+                        const int t0 = c * Z + j - lo, t1 = t0 + H;
+                        const uint32_t b0 =
+                            (t0 >= 0 && t0 < p.n_tx) ? ((uint32_t)(uint8_t)src[t0] ^ 0x80u) : 0x80u;
+                        const uint32_t b1 =
+                            (t1 >= 0 && t1 < p.n_tx) ? ((uint32_t)(uint8_t)src[t1] ^ 0x80u) : 0x80u;
+                        Lb[c * H + j] = 0x64006400u | b0 | (b1 << 16);
+                    }
+                }
+                named_sync(bar_id, nthr_half);
+                // the staging buffer is free: start the copy of this half's next codeword
+                if (pp.use_tma && ht == 0 && cw + stride < p.batch)
+                    bulk_load(const_cast<int8_t *>(stage), llr_all + (size_t)(cw + stride) * p.n_tx,
+                              (uint32_t)p.n_tx, bar);
+
+                int done = p.max_iter;
+#pragma unroll 1
+                for (int t = 1; t <= p.max_iter; ++t) {
+#pragma unroll 1
+                    for (int r = 0; r < n_rows; ++r) {
                         const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
-                        bad = __any_sync(0xffffffffu, tm_parity(pp, Lb, e0, d, H, w) != 0u);
+                        tm_dispatch(d, s_meta, Lb, tbase, e0, H, w, store);
+                        named_sync(bar_id, nthr_half);
                     }
-                    if (named_or(bar_id, nthr_half, bad) == 0) {
-                        done = t;
-                        break;
+                    if (p.early_stop) {
+                        int bad = 0;
+                        for (int r = 0; r < n_rows && !bad; ++r) {
+                            const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
+                            bad = __any_sync(0xffffffffu,
+                                             tm_parity(s_meta, Lb, e0, d, H, w) != 0u);
+                        }
+                        if (named_or(bar_id, nthr_half, bad) == 0) {
+                            done = t;
+                            break;
+                        }
                     }
                 }
-            }
 
-            // a6: outputs
-            for (int b = ht; b < nbytes; b += nthr_half) {
-                unsigned x = 0;
-                for (int kk = 0; kk < 8; ++kk) {
-                    const int j = 8 * b + kk;
-                    if (j >= K) break;
-                    const int c = j / Z, i = j - c * Z;
-                    const int lane = i >= H ? 1 : 0;
-                    const uint32_t wd = Lb[c * H + i - lane * H];
-                    const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-                    if (h < 0x6480u) x |= 1u << kk;
-                }
-                p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
-            }
-            if (ht == 0) p.iters[cw] = done;
-            if (p.post) {
-                int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw * n_cols * Z;
-                for (int c = 0; c < n_cols; ++c)
-                    for (int i = ht; i < Z; i += nthr_half) {
+                // a6: outputs
+                for (int b = ht; b < nbytes; b += nthr_half) {
+                    unsigned x = 0;
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const int j = 8 * b + kk;
+                        if (j >= K) break;
+                        const int c = j / Z, i = j - c * Z;
                         const int lane = i >= H ? 1 : 0;
                         const uint32_t wd = Lb[c * H + i - lane * H];
                         const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-                        po[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
+                        if (h < 0x6480u) x |= 1u << kk;
                     }
-            }
-            if (p.c2v) {
-                // each thread reads its own TMEM lane: messages of rows w and w + H
-                twait_st();
-                int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * E * Z;
-                for (int e = 0; e < E; ++e) {
-                    uint32_t v;
-                    tld<1>(tbase + (uint32_t)(e >> 1), &v);
-                    twait_ld();
-                    const uint32_t pr = (e & 1) ? (v >> 16) : (v & 0xffffu);
-                    if (store) {
-                        co[e * Z + w] = (int8_t)(uint8_t)((pr & 0xffu) ^ 0x80u);
-                        co[e * Z + w + H] = (int8_t)(uint8_t)(((pr >> 8) & 0xffu) ^ 0x80u);
+                    p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
+                }
+                if (ht == 0) p.iters[cw] = done;
+                if (p.post) {
+                    int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw * n_cols * Z;
+                    for (int c = 0; c < n_cols; ++c)
+                        for (int i = ht; i < Z; i += nthr_half) {
+                            const int lane = i >= H ? 1 : 0;
+                            const uint32_t wd = Lb[c * H + i - lane * H];
+                            const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                            po[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
+                        }
+                }
+                if (p.c2v) {
+                    // each thread reads its own TMEM lane: messages of rows w and w + H
+                    twait_st();
+                    int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * E * Z;
+                    for (int e = 0; e < E; ++e) {
+                        uint32_t v;
+                        tld<1>(tbase + (uint32_t)(e >> 1), &v);
+                        twait_ld();
+                        const uint32_t pr = (e & 1) ? (v >> 16) : (v & 0xffffu);
+                        if (store) {
+                            co[e * Z + w] = (int8_t)(uint8_t)((pr & 0xffu) ^ 0x80u);
+                            co[e * Z + w + H] =
+                                (int8_t)(uint8_t)(((pr >> 8) & 0xffu) ^ 0x80u);
+                        }
                     }
                 }
             }
         }
         named_sync(bar_id, nthr_half);
     }
+    // a copy that never completed must not outlive the block: wait for it (bounded)
+    if (failed && ht == 0) mbar_wait(bar, parity);
 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -398,7 +474,9 @@ bool tmem_supported(const DecodeParams &p, int llr_type, int max_deg, size_t sme
     const int H = p.Z / 2, wpc = (H + 31) / 32;
     const int depth = (2 * wpc + 3) / 4;
     if (depth * tmem_columns_per_thread(p) > kTmemCols) return false;
-    return (size_t)2 * p.n_cols * H * 4 <= smem_optin;
+    const size_t need = (size_t)p.E * sizeof(EdgeMetaT) + 32 + (size_t)2 * p.n_cols * H * 4 +
+                        2 * (size_t)p.n_tx + 64;
+    return need <= smem_optin;
 }
 
 ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream) {
@@ -418,9 +496,17 @@ ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream) {
         pp.meta[e].sel_nw = q ? 0x1032u : 0x3210u;
         pp.meta[e].sel_w = q ? 0x3210u : 0x1032u;
     }
-    // two posterior arrays; at least 120 kB so that a single block occupies the SM (its TMEM
-    // allocation takes all 512 columns)
-    size_t smem = (size_t)2 * p.n_cols * H * 4;
+    // shared memory: metadata | two posterior arrays | two LLR staging buffers; at least
+    // 120 kB so that a single block occupies the SM (its TMEM allocation takes all 512
+    // columns).  Bulk copies need 16-byte aligned rows.
+    pp.use_tma = ((reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0 && (p.n_tx % 16) == 0 &&
+                  p.n_tx > 0 && p.n_tx < (1 << 20))
+                     ? 1
+                     : 0;
+    pp.stage_bytes = pp.use_tma ? p.n_tx : 0;
+    pp.off_lb = (int)(((size_t)p.E * sizeof(EdgeMetaT) + 15) & ~(size_t)15);
+    pp.off_stage = (pp.off_lb + 2 * p.n_cols * H * 4 + 15) & ~15;
+    size_t smem = (size_t)pp.off_stage + 2 * (size_t)pp.stage_bytes;
     if (smem < 120 * 1024) smem = 120 * 1024;
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;

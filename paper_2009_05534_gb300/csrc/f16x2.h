@@ -66,6 +66,12 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(s));
     return d;
 }
+// |a| per lane (a sign-bit clear; foldable into a following add as an operand modifier)
+__device__ __forceinline__ uint32_t h2abs(uint32_t a) {
+    uint32_t d;
+    asm("abs.f16x2 %0, %1;" : "=r"(d) : "r"(a));
+    return d;
+}
 // per-lane (a < b) of binary16 values -> 0xFFFF / 0 per lane
 __device__ __forceinline__ uint32_t h2lt_mask(uint32_t a, uint32_t b) {
     uint32_t d;
