@@ -31,6 +31,7 @@ if ROOT not in sys.path:
 KIND, Z, EBN0, BATCH, T_ITER, SEED = "BG1", 384, 1.5, 1024, 10, 0
 WORKLOAD = "BG1-shaped 46x68 Z=384 K=8448 R=1/3 QPSK AWGN Eb/N0=1.5dB int8 offset-1 min-sum T=10"
 L2_BYTES = 129 * 2 ** 20
+METRIC = "decoded information throughput (BG1 Z=384, 10 it)"
 
 
 def parse():
@@ -41,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-slots", type=int, default=2000,
+                    help="slots of the mixed-traffic serving measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -164,6 +167,68 @@ def profiled_traffic(kernel_tag: str):
     return got if (got is not None and sha == h) else None
 
 
+# ------------------------------------------------------------------------- slot serving
+
+SERVE_ZS = (32, 64, 96, 128, 192, 256, 384)
+SERVE_RATES = ("1/3", "1/2", "2/3", "5/6", "8/9")
+SERVE_MODS = (("QPSK", 3.0), ("16QAM", 7.0), ("64QAM", 11.0))
+
+
+def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_iter: int = 10):
+    """Mixed-traffic slot serving: Poisson(mean_tbs) transport blocks per 500 us slot
+    (clipped to 64..512), each a uniformly drawn (BG1|BG2, Z, rate, modulation) codeword
+    from a device-resident pool of synthetic int8 LLRs; returns p50/p99 latency and
+    throughput."""
+    from fractions import Fraction
+
+    import numpy as np
+    import torch
+
+    import paper_2009_05534_gb300 as ldpc
+    from paper_2009_05534_gb300.serve import GpuBackend, SlotScheduler, latency_stats, run_paced
+    from synth import make_workload
+    rng = np.random.default_rng(seed)
+    graphs, rows, ks, llrs = {}, [], [], []
+    for kind in ("BG1", "BG2"):
+        for Zs in SERVE_ZS:
+            for rate in SERVE_RATES:
+                for m, (mod, eb) in enumerate(SERVE_MODS):
+                    wl = make_workload(kind, Zs, 2, eb, rate=Fraction(rate), modulation=mod,
+                                       seed=seed * 1000 + len(rows))
+                    if (kind, Zs) not in graphs:
+                        graphs[(kind, Zs)] = ldpc.Graph(wl.base, wl.K_b, Zs)
+                    q = torch.from_numpy(wl.llr_int8()).cuda()
+                    for b in range(2):
+                        llrs.append(q[b])
+                        rows.append((graphs[(kind, Zs)].handle.value, q[b].data_ptr(), 0, 0,
+                                     wl.n_rows, wl.n_tx, max_iter))
+                        ks.append(wl.K)
+    pool = np.array(rows, dtype=ldpc.work_item_dtype)
+    ks = np.array(ks, np.int64)
+    counts = np.clip(rng.poisson(mean_tbs, size=n_slots), 64, 512)
+    total = int(counts.sum())
+    pick = rng.integers(0, len(pool), size=total)
+    table, kreq = pool[pick], ks[pick]
+    kmax = max(g.K for g in graphs.values())
+    be = GpuBackend(table, kreq, n_buffers=4096, kmax=kmax, n_streams=4, early_stop=True)
+    sch = SlotScheduler(be, slot_us=500.0, max_requests=total + 1)
+    # warm-up: a few slots outside the measurement
+    warm = SlotScheduler(GpuBackend(pool, ks, n_buffers=1024, kmax=kmax), slot_us=500.0,
+                         max_requests=4096)
+    run_paced(warm, [min(len(pool), 512)] * 3)
+    torch.cuda.synchronize()
+    wall = run_paced(sch, counts.tolist(), 500.0)
+    st = latency_stats(sch.completed_latencies())
+    for g in graphs.values():
+        g.close()
+    del llrs
+    return {"slots": n_slots, "slot_us": 500.0, "tbs": total, "mean_tbs_per_slot":
+            float(counts.mean()), "p50_us": st.get("p50_us"), "p99_us": st.get("p99_us"),
+            "max_us": st.get("max_us"), "gbps": float(kreq.sum()) / wall / 1e9,
+            "max_iter": max_iter, "early_stop": True,
+            "traffic": "BG1|BG2 x Z{32..384} x R{1/3..8/9} x QPSK/16QAM/64QAM int8"}
+
+
 # ----------------------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -188,7 +253,7 @@ def run_reference(args):
     tot = sum(times)
     val = n * wl.K * args.steps / tot / 1e9
     line = {
-        "impl": "reference", "metric": "decoded information throughput", "value": val,
+        "impl": "reference", "metric": METRIC, "value": val,
         "unit": "Gbit/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
@@ -319,6 +384,8 @@ def run_ours(args):
     alg_bytes = B * (wl.n_tx + nbytes + 4)
     traffic = profiled_traffic("layered_int8_bg1_z384")
 
+    serving = serving_measure(args.serve_slots) if args.serve_slots > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -328,7 +395,7 @@ def run_ours(args):
                          f"decoded repeatedly ({done} codewords in {el:.1f} s, {cpu_model()})"}
     if rank == 0:
         line = {
-            "metric": "decoded information throughput (BG1 Z=384, 10 it)",
+            "metric": METRIC,
             "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -349,6 +416,7 @@ def run_ours(args):
                            "ebn0_db": EBN0},
             "e2e": {"value": e2e, "unit": "Gbit/s", "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": B * (nbytes + 4)},
+            "serving": serving,
             "gpu_launches": launches,
             "clocks": clocks,
             "wall_s": t_wall,

@@ -140,6 +140,34 @@ ldpc_status ldpc_decode_host(ldpc_graph_t g, const void *llr_host, int batch, in
                              ldpc_stream_t stream, const ldpc_decode_opts *opts,
                              uint8_t *hard_bits_host, int32_t *iters_host);
 
+/* One codeword of a heterogeneous work list (ldpc_decode_list).
+ *   graph       its graph (any mix of graphs, lifting sizes and row counts in one list)
+ *   llr         device [n_tx] int8 channel LLRs
+ *   hard_bits   device uint8 [ceil(K_b*Z/8)] output (LSB-first)
+ *   iters       device int32 [1] output
+ *   n_rows      base rows used (0 = all); n_tx: transmitted LLRs (0 = from n_rows);
+ *   max_iter    iteration cap, 1..64. */
+typedef struct {
+    ldpc_graph_t graph;
+    const void *llr;
+    uint8_t *hard_bits;
+    int32_t *iters;
+    int n_rows;
+    int n_tx;
+    int max_iter;
+} ldpc_work_item;
+
+/* Decode a heterogeneous list of codewords in one launch (Sec. III decoding, Sec. IV many
+ * codewords in parallel; the serving path).  int8 offset min-sum with offset_q = 1 and
+ * punct_cols = 2 (opts: early_stop is honoured, llr_type must be INT8, algo OFFSET).
+ * Each item needs even Z <= 384 and row degrees 2..20 (LDPC_ERR_UNSUPPORTED otherwise).
+ * Thread blocks take items dynamically, largest first.  The library keeps a per-stream
+ * device work table and work counter (allocated on first use, grown on demand, released
+ * at exit); the host item array is copied before the call returns, so it may be reused.
+ * Asynchronous on `stream`. */
+ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stream_t stream,
+                             const ldpc_decode_opts *opts);
+
 /* Wait for the graph's outstanding work on `stream` and return (then clear) the device
  * status word: LDPC_OK, or the first error a kernel reported (e.g. LDPC_ERR_TIMEOUT). */
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t g, ldpc_stream_t stream);

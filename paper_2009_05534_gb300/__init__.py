@@ -30,6 +30,12 @@ class LdpcError(RuntimeError):
         self.status = status
 
 
+class WorkItem(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("llr", ctypes.c_void_p),
+                ("hard_bits", ctypes.c_void_p), ("iters", ctypes.c_void_p),
+                ("n_rows", ctypes.c_int), ("n_tx", ctypes.c_int), ("max_iter", ctypes.c_int)]
+
+
 class DecodeOpts(ctypes.Structure):
     _fields_ = [("llr_type", ctypes.c_int), ("algo", ctypes.c_int), ("alpha", ctypes.c_float),
                 ("offset", ctypes.c_float), ("offset_q", ctypes.c_int), ("n_rows", ctypes.c_int),
@@ -45,7 +51,7 @@ _lock = threading.Lock()
 ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_destroy",
                "ldpc_graph_edges", "ldpc_graph_vars", "ldpc_decode", "ldpc_decode_debug",
                "ldpc_graph_sync_status", "ldpc_status_string", "ldpc_launch_count",
-               "ldpc_decode_host")
+               "ldpc_decode_host", "ldpc_decode_list")
 
 
 def lib():
@@ -75,6 +81,9 @@ def lib():
             L.ldpc_decode_debug.restype = i
             L.ldpc_decode_host.argtypes = [P, P, i, i, P, ctypes.POINTER(DecodeOpts), P, P]
             L.ldpc_decode_host.restype = i
+            L.ldpc_decode_list.argtypes = [ctypes.POINTER(WorkItem), i, P,
+                                           ctypes.POINTER(DecodeOpts)]
+            L.ldpc_decode_list.restype = i
             L.ldpc_graph_sync_status.argtypes = [P, P]
             L.ldpc_graph_sync_status.restype = i
             L.ldpc_status_string.argtypes = [i]
@@ -234,6 +243,39 @@ def decode_host(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stre
                                   ctypes.c_void_p(bits.data_ptr()),
                                   ctypes.c_void_p(iters.data_ptr())), "ldpc_decode_host")
     return bits, iters
+
+
+# numpy record layout of ldpc_work_item (pointers as uint64), for building work lists
+# without per-item Python objects
+work_item_dtype = np.dtype({
+    "names": ["graph", "llr", "hard_bits", "iters", "n_rows", "n_tx", "max_iter"],
+    "formats": [np.uint64, np.uint64, np.uint64, np.uint64, np.int32, np.int32, np.int32],
+    "offsets": [WorkItem.graph.offset, WorkItem.llr.offset, WorkItem.hard_bits.offset,
+                WorkItem.iters.offset, WorkItem.n_rows.offset, WorkItem.n_tx.offset,
+                WorkItem.max_iter.offset],
+    "itemsize": ctypes.sizeof(WorkItem)})
+
+
+def decode_list_array(items: np.ndarray, *, stream=None, early_stop=True):
+    """ldpc_decode_list on a numpy record array of ``work_item_dtype`` (asynchronous)."""
+    arr = np.ascontiguousarray(items, dtype=work_item_dtype)
+    o = make_opts(LLR_INT8, early_stop=early_stop)
+    _check(lib().ldpc_decode_list(arr.ctypes.data_as(ctypes.POINTER(WorkItem)), len(arr),
+                                  _stream_ptr(stream), ctypes.byref(o)), "ldpc_decode_list")
+
+
+def decode_list(items, *, stream=None, early_stop=True):
+    """Decode a heterogeneous list in one launch (ldpc_decode_list).
+
+    items: sequence of (graph, llr int8 CUDA tensor [n_tx], bits uint8 CUDA tensor
+    [ceil(K/8)], iters int32 CUDA tensor [1], n_rows, n_tx, max_iter).  Outputs are written
+    in place; the call is asynchronous on the stream.
+    """
+    arr = np.zeros(len(items), dtype=work_item_dtype)
+    for k, (g, llr, bits, it, n_rows, n_tx, max_iter) in enumerate(items):
+        arr[k] = (g.handle.value, llr.data_ptr(), bits.data_ptr(), it.data_ptr(), int(n_rows),
+                  int(n_tx), int(max_iter))
+    decode_list_array(arr, stream=stream, early_stop=early_stop)
 
 
 def unpack_bits(packed: np.ndarray, K: int) -> np.ndarray:

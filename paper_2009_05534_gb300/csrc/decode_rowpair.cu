@@ -1,8 +1,10 @@
-// Row-pair fp16x2 layered min-sum kernel for 8-bit offset min-sum (sm_103a).
+// Row-pair fp16x2 layered min-sum for 8-bit offset min-sum, messages in shared memory
+// (sm_103a).  Used by the batch decode when the Tensor-Memory kernel does not take the shape,
+// and by the work-list decode, which decodes a heterogeneous list of codewords (different
+// graphs, lifting sizes and rates) in one launch.
 //
 // Same method as the generic kernel (paper Sec. III layered min-sum with correction,
-// Sec. IV per-row m1 / m2 / sign quantities, a1..a6 of the hot path), mapped for
-// throughput on GB300:
+// Sec. IV per-row m1 / m2 / sign quantities, hot-path steps a0..a6), mapped for GB300:
 //
 // * Lanes.  Check rows i and i + H (H = Z/2) of a layer travel together in one 32-bit
 //   register as two binary16 lanes.  The 8-bit LLRs are integers in [-127, 127]; every
@@ -22,8 +24,8 @@
 //   instruction; m2 follows from max.xorsign / min.xorsign.  The new message magnitude
 //   uses  excl = max(m1', (m1 + m2 - offset) - |v|): it equals m2' on the argmin edge and
 //   m1' elsewhere (ties give m2 = m1), so no argmin index is needed on the forward pass.
-// * Two threads share a row pair (edges split even / odd) and merge their partial
-//   m1 / m2 / sign with one shuffle exchange.
+// * One thread owns one row pair of every layer; the per-edge gather metadata sits in
+//   shared memory and is read with one broadcast 16-byte load per edge.
 #include "f16x2.h"
 #include "ldpc_internal.h"
 
@@ -32,8 +34,7 @@ namespace {
 
 using namespace h2;
 
-// Per-edge gather metadata for row pair j of a layer (kernel parameters, so the warp-uniform
-// edge index turns into constant-bank loads):
+// Per-edge gather metadata for row pair j of a layer:
 //   word = j + base_nw            if j <  thresh   (no wrap), halves permuted by sel_nw
 //   word = j + base_nw - H        if j >= thresh   (wrap),    halves permuted by sel_w
 struct EdgeMeta {
@@ -43,32 +44,49 @@ struct EdgeMeta {
     uint32_t sel_w;
 };
 
+__host__ __device__ __forceinline__ EdgeMeta make_meta(uint32_t edge, int H) {
+    const int c = (int)(edge >> 16), sh = (int)(edge & 0xffffu);
+    const int q = sh >= H ? 1 : 0, u = sh - q * H;
+    EdgeMeta m;
+    m.base_nw = c * H + u;
+    m.thresh = H - u;
+    m.sel_nw = q ? 0x1032u : 0x3210u;
+    m.sel_w = q ? 0x3210u : 0x1032u;
+    return m;
+}
+
 constexpr int kMaxEdgesP = 1024;
 constexpr int kMaxRowsP = 64;
+constexpr int kThreadsP = 192;      // one thread per row pair, Z <= 384
 
-struct PairParams {
-    DecodeParams p;
-    int H;
-    int row[kMaxRowsP + 1];
-    EdgeMeta meta[kMaxEdgesP];
+// Everything one codeword's decode needs.
+struct CwArgs {
+    int Z, H, K_b, n_rows, n_cols, E;
+    int punct, n_tx, max_iter, early_stop;
+    const int8_t *llr;     // [n_tx]
+    uint8_t *bits;         // [ceil(K/8)]
+    int32_t *iters;        // [1]
+    int8_t *post;          // [n_cols * Z] or null
+    int8_t *c2v;           // [E * Z] or null
 };
 
 struct Smem {
-    uint32_t *Lb;        // [n_cols][H] words
-    uint16_t *c2v;       // [E][H] byte pairs
+    const EdgeMeta *meta;   // [E]
+    const int *row;         // [n_rows + 1]
+    uint32_t *Lb;           // [n_cols][H] words
+    uint16_t *c2v;          // [E][H] byte pairs
 };
 
 // One thread owns row pair w of every layer; D is the row degree (straight-line code).
 template <int D>
-__device__ __forceinline__ void process_row(const PairParams &pp, const Smem &s, int e0, int H,
-                                            int w, bool store) {
+__device__ __forceinline__ void process_row(const Smem &s, int e0, int H, int w, bool store) {
     uint32_t v[D];
     int addr[D];
     uint32_t sel[D];
     uint32_t m1 = kInf2, m2 = kInf2;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const EdgeMeta &mt = pp.meta[e0 + j];
+        const EdgeMeta mt = s.meta[e0 + j];
         const bool wr = w >= mt.thresh;
         const int a = w + mt.base_nw - (wr ? H : 0);
         const uint32_t sl = wr ? mt.sel_w : mt.sel_nw;
@@ -90,7 +108,7 @@ __device__ __forceinline__ void process_row(const PairParams &pp, const Smem &s,
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const uint32_t x = v[j];
-        const uint32_t ex = h2max(m1c, h2sub(T1, x & kAbs2));
+        const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
         const uint32_t sg = (x & kSign2) ^ SO;                 // S xor sgn(x), as +-1.0
         const uint32_t Cm = h2fma(ex, sg, kBias2);             // c' + 1152
         uint32_t Lb = h2add(Cm, x);                            // (x + c') + 1152
@@ -102,12 +120,12 @@ __device__ __forceinline__ void process_row(const PairParams &pp, const Smem &s,
     }
 }
 
-__device__ __forceinline__ void dispatch_row(int d, const PairParams &pp, const Smem &s, int e0,
-                                             int H, int w, bool store) {
+__device__ __forceinline__ void dispatch_row(int d, const Smem &s, int e0, int H, int w,
+                                             bool store) {
     switch (d) {
 #define LDPC_ROW_CASE(D) \
     case D:              \
-        process_row<D>(pp, s, e0, H, w, store); \
+        process_row<D>(s, e0, H, w, store); \
         break;
         LDPC_ROW_CASE(2) LDPC_ROW_CASE(3) LDPC_ROW_CASE(4) LDPC_ROW_CASE(5) LDPC_ROW_CASE(6)
         LDPC_ROW_CASE(7) LDPC_ROW_CASE(8) LDPC_ROW_CASE(9) LDPC_ROW_CASE(10) LDPC_ROW_CASE(11)
@@ -121,139 +139,202 @@ __device__ __forceinline__ void dispatch_row(int d, const PairParams &pp, const 
 }
 
 // parity of the hard decisions (L < 0  <=>  biased value < 1152) of row pair w
-__device__ __forceinline__ uint32_t row_parity(const PairParams &pp, const Smem &s, int e0,
-                                               int d, int H, int w) {
+__device__ __forceinline__ uint32_t row_parity(const Smem &s, int e0, int d, int H, int w) {
     uint32_t par = 0;
     for (int j = 0; j < d; ++j) {
-        const EdgeMeta &mt = pp.meta[e0 + j];
+        const EdgeMeta mt = s.meta[e0 + j];
         const bool wr = w >= mt.thresh;
         const int a = w + mt.base_nw - (wr ? H : 0);
-        const uint32_t X = prmt(s.Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw);
-        par ^= h2lt_mask(X, kBias2);
+        par ^= h2lt_mask(prmt(s.Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kBias2);
     }
     return par;
 }
 
-__global__ void __launch_bounds__(256, 1) rowpair_kernel(const __grid_constant__ PairParams pp) {
-    const DecodeParams &p = pp.p;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
-    Smem s;
-    s.Lb = reinterpret_cast<uint32_t *>(smem);
-    s.c2v = reinterpret_cast<uint16_t *>(smem + (size_t)n_cols * H * 4);
-
+// Decode one codeword with the whole block (blockDim.x >= H threads; the graph metadata is
+// already in shared memory).  Starts and ends with the block synchronised.
+__device__ void decode_codeword(const CwArgs &a, const Smem &s) {
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // threads past the last row pair repeat its work and store nothing
+    const int Z = a.Z, H = a.H, E = a.E, n_cols = a.n_cols;
     const bool store = tid < H;
-    const int w = store ? tid : H - 1;
-    const int K = p.K_b * Z;
-    const int nbytes = (K + 7) >> 3;
-    const int lo = p.punct * Z;
-    const int8_t *llr_all = reinterpret_cast<const int8_t *>(p.llr);
+    const int w = store ? tid : H - 1;       // spare threads shadow the last row pair
+    const int lo = a.punct * Z;
 
-    for (int cw = blockIdx.x; cw < p.batch; cw += gridDim.x) {
-        // a0: biased posteriors from the channel LLRs (0 -> 1152 for punctured / unsent
-        // bits), messages zero (stored as 0x80)
-        const int8_t *llr = llr_all + (size_t)cw * p.n_tx;
-        for (int i = tid; i < n_cols * H; i += nthr) s.Lb[i] = 0x64806480u;
-        {
-            uint32_t *c2 = reinterpret_cast<uint32_t *>(s.c2v);
-            const int nw = (E * H) >> 1;
-            for (int i = tid; i < nw; i += nthr) c2[i] = 0x80808080u;
-            if ((E * H) & 1)
-                if (tid == 0) s.c2v[E * H - 1] = 0x8080u;
+    // a0: biased posteriors from the channel LLRs, zero messages (stored as 0x80)
+    for (int c = 0; c < n_cols; ++c)
+        for (int j = tid; j < H; j += nthr) {
+            const int t0 = c * Z + j - lo, t1 = t0 + H;
+            const uint32_t b0 =
+                (t0 >= 0 && t0 < a.n_tx) ? ((uint32_t)(uint8_t)a.llr[t0] ^ 0x80u) : 0x80u;
+            const uint32_t b1 =
+                (t1 >= 0 && t1 < a.n_tx) ? ((uint32_t)(uint8_t)a.llr[t1] ^ 0x80u) : 0x80u;
+            s.Lb[c * H + j] = 0x64006400u | b0 | (b1 << 16);
         }
-        __syncthreads();
-        {
-            uint16_t *Lh = reinterpret_cast<uint16_t *>(s.Lb);
-#pragma unroll 8
-            for (int t = tid; t < p.n_tx; t += nthr) {
-                const int j = lo + t;
-                const int c = j / Z, i = j - c * Z;
-                const int lane = i >= H ? 1 : 0;
-                Lh[2 * (c * H + i - lane * H) + lane] =
-                    (uint16_t)(0x6400u | ((uint32_t)(uint8_t)llr[t] ^ 0x80u));
-            }
-        }
-        __syncthreads();
+    {
+        uint32_t *c2 = reinterpret_cast<uint32_t *>(s.c2v);
+        const int nw = (E * H) >> 1;
+        for (int i = tid; i < nw; i += nthr) c2[i] = 0x80808080u;
+        if (((E * H) & 1) && tid == 0) s.c2v[E * H - 1] = 0x8080u;
+    }
+    __syncthreads();
 
-        int done = p.max_iter;
+    int done = a.max_iter;
 #pragma unroll 1
-        for (int t = 1; t <= p.max_iter; ++t) {
+    for (int t = 1; t <= a.max_iter; ++t) {
 #pragma unroll 1
-            for (int r = 0; r < n_rows; ++r) {
-                const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
-                dispatch_row(d, pp, s, e0, H, w, store);
-                __syncthreads();
+        for (int r = 0; r < a.n_rows; ++r) {
+            const int e0 = s.row[r], d = s.row[r + 1] - e0;
+            dispatch_row(d, s, e0, H, w, store);
+            __syncthreads();
+        }
+        if (a.early_stop) {
+            int bad = 0;
+            for (int r = 0; r < a.n_rows && !bad; ++r) {
+                const int e0 = s.row[r], d = s.row[r + 1] - e0;
+                bad = __any_sync(0xffffffffu, row_parity(s, e0, d, H, w) != 0u);
             }
-            if (p.early_stop) {
-                int bad = 0;
-                for (int r = 0; r < n_rows; ++r) {
-                    const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
-                    const uint32_t par = row_parity(pp, s, e0, d, H, w);
-                    bad = __any_sync(0xffffffffu, par != 0u);
-                    if (bad) break;
-                }
-                if (__syncthreads_or(bad) == 0) {
-                    done = t;
-                    break;
-                }
+            if (__syncthreads_or(bad) == 0) {
+                done = t;
+                break;
             }
         }
+    }
 
-        // a6: hard bits of the K information bits, LSB first
-        for (int b = tid; b < nbytes; b += nthr) {
-            unsigned x = 0;
-            for (int kk = 0; kk < 8; ++kk) {
-                const int j = 8 * b + kk;
-                if (j >= K) break;
-                const int c = j / Z, i = j - c * Z;
+    // a6: hard bits of the K information bits, LSB first; iteration count
+    const int K = a.K_b * Z, nbytes = (K + 7) >> 3;
+    for (int b = tid; b < nbytes; b += nthr) {
+        unsigned x = 0;
+        for (int kk = 0; kk < 8; ++kk) {
+            const int j = 8 * b + kk;
+            if (j >= K) break;
+            const int c = j / Z, i = j - c * Z;
+            const int lane = i >= H ? 1 : 0;
+            const uint32_t wd = s.Lb[c * H + i - lane * H];
+            const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+            if (h < 0x6480u) x |= 1u << kk;
+        }
+        a.bits[b] = (uint8_t)x;
+    }
+    if (tid == 0) a.iters[0] = done;
+    if (a.post)
+        for (int c = 0; c < n_cols; ++c)
+            for (int i = tid; i < Z; i += nthr) {
                 const int lane = i >= H ? 1 : 0;
                 const uint32_t wd = s.Lb[c * H + i - lane * H];
                 const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-                if (h < 0x6480u) x |= 1u << kk;
+                a.post[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
             }
-            p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
-        }
-        if (tid == 0) p.iters[cw] = done;
-        if (p.post) {
-            int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw * n_cols * Z;
-            for (int c = 0; c < n_cols; ++c)
-                for (int i = tid; i < Z; i += nthr) {
-                    const int lane = i >= H ? 1 : 0;
-                    const uint32_t wd = s.Lb[c * H + i - lane * H];
-                    const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-                    po[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
-                }
-        }
-        if (p.c2v) {
-            int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * E * Z;
-            for (int e = 0; e < E; ++e)
-                for (int i = tid; i < Z; i += nthr) {
-                    const int lane = i >= H ? 1 : 0;
-                    const uint32_t pr = s.c2v[e * H + i - lane * H];
-                    const uint32_t b = lane ? (pr >> 8) : (pr & 0xffu);
-                    co[e * Z + i] = (int8_t)(uint8_t)((b & 0xffu) ^ 0x80u);
-                }
-        }
+    if (a.c2v)
+        for (int e = 0; e < E; ++e)
+            for (int i = tid; i < Z; i += nthr) {
+                const int lane = i >= H ? 1 : 0;
+                const uint32_t pr = s.c2v[e * H + i - lane * H];
+                const uint32_t b = lane ? (pr >> 8) : (pr & 0xffu);
+                a.c2v[e * Z + i] = (int8_t)(uint8_t)((b & 0xffu) ^ 0x80u);
+            }
+    __syncthreads();
+}
+
+// shared-memory carve-up: metadata | row pointers | posteriors | messages
+__host__ __device__ __forceinline__ size_t smem_layout(int E, int n_rows, int n_cols, int H,
+                                                       size_t *off_row, size_t *off_lb,
+                                                       size_t *off_c2v) {
+    size_t off = (size_t)E * sizeof(EdgeMeta);
+    *off_row = off;
+    off += (size_t)(n_rows + 1) * 4;
+    off = (off + 15) & ~(size_t)15;
+    *off_lb = off;
+    off += (size_t)n_cols * H * 4;
+    *off_c2v = off;
+    off += (size_t)E * H * 2;
+    return (off + 15) & ~(size_t)15;
+}
+
+// ----------------------------------------------------------------------- batch kernel
+
+struct PairParams {
+    DecodeParams p;
+    int H;
+    int row[kMaxRowsP + 1];
+    EdgeMeta meta[kMaxEdgesP];
+};
+
+__global__ void __launch_bounds__(kThreadsP, 1) rowpair_kernel(const __grid_constant__ PairParams pp) {
+    const DecodeParams &p = pp.p;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int H = pp.H;
+    size_t off_row, off_lb, off_c2v;
+    smem_layout(p.E, p.n_rows, p.n_cols, H, &off_row, &off_lb, &off_c2v);
+    EdgeMeta *s_meta = reinterpret_cast<EdgeMeta *>(smem);
+    int *s_row = reinterpret_cast<int *>(smem + off_row);
+    for (int e = threadIdx.x; e < p.E; e += blockDim.x) s_meta[e] = pp.meta[e];
+    for (int r = threadIdx.x; r <= p.n_rows; r += blockDim.x) s_row[r] = pp.row[r];
+    Smem s{s_meta, s_row, reinterpret_cast<uint32_t *>(smem + off_lb),
+           reinterpret_cast<uint16_t *>(smem + off_c2v)};
+    __syncthreads();
+    const int nbytes = (p.K_b * p.Z + 7) >> 3;
+    for (int cw = blockIdx.x; cw < p.batch; cw += gridDim.x) {
+        CwArgs a;
+        a.Z = p.Z; a.H = H; a.K_b = p.K_b; a.n_rows = p.n_rows; a.n_cols = p.n_cols; a.E = p.E;
+        a.punct = p.punct; a.n_tx = p.n_tx; a.max_iter = p.max_iter; a.early_stop = p.early_stop;
+        a.llr = reinterpret_cast<const int8_t *>(p.llr) + (size_t)cw * p.n_tx;
+        a.bits = p.bits + (size_t)cw * nbytes;
+        a.iters = p.iters + cw;
+        a.post = p.post ? reinterpret_cast<int8_t *>(p.post) + (size_t)cw * p.n_cols * p.Z : nullptr;
+        a.c2v = p.c2v ? reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * p.E * p.Z : nullptr;
+        decode_codeword(a, s);
+    }
+}
+
+// ------------------------------------------------------------------- work-list kernel
+
+__global__ void __launch_bounds__(kThreadsP, 1)
+    list_kernel(const ListItem *__restrict__ items, int n_items, int *counter, int early_stop) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(counter, 1);
         __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= n_items) break;
+        const ListItem it = items[idx];
+        const int H = it.Z / 2;
+        size_t off_row, off_lb, off_c2v;
+        smem_layout(it.E, it.n_rows, it.n_cols, H, &off_row, &off_lb, &off_c2v);
+        EdgeMeta *s_meta = reinterpret_cast<EdgeMeta *>(smem);
+        int *s_row = reinterpret_cast<int *>(smem + off_row);
+        for (int e = threadIdx.x; e < it.E; e += blockDim.x) s_meta[e] = make_meta(it.edges[e], H);
+        for (int r = threadIdx.x; r <= it.n_rows; r += blockDim.x) s_row[r] = it.row_ptr[r];
+        __syncthreads();
+        Smem s{s_meta, s_row, reinterpret_cast<uint32_t *>(smem + off_lb),
+               reinterpret_cast<uint16_t *>(smem + off_c2v)};
+        CwArgs a;
+        a.Z = it.Z; a.H = H; a.K_b = it.K_b; a.n_rows = it.n_rows; a.n_cols = it.n_cols;
+        a.E = it.E; a.punct = it.punct; a.n_tx = it.n_tx; a.max_iter = it.max_iter;
+        a.early_stop = early_stop;
+        a.llr = it.llr; a.bits = it.bits; a.iters = it.iters; a.post = nullptr; a.c2v = nullptr;
+        decode_codeword(a, s);
     }
 }
 
 }  // namespace
 
 size_t rowpair_smem_bytes(int E, int n_rows, int n_cols, int Z) {
-    (void)n_rows;
-    const int H = Z / 2;
-    size_t off = (size_t)n_cols * H * 4 + (size_t)E * H * 2;
-    return (off + 15) & ~(size_t)15;
+    size_t a, b, c;
+    return smem_layout(E, n_rows, n_cols, Z / 2, &a, &b, &c);
 }
 
 bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin) {
     if (llr_type != LDPC_LLR_INT8 || p.algo != LDPC_OFFSET || p.offset_q != 1) return false;
-    if ((p.Z & 1) || p.Z < 2 || p.Z > 512 || max_deg > kMaxDeg || max_deg < 2) return false;
+    if ((p.Z & 1) || p.Z < 2 || p.Z > 2 * kThreadsP || max_deg > kMaxDeg || max_deg < 2)
+        return false;
     if (p.E > kMaxEdgesP || p.n_rows > kMaxRowsP) return false;
     return rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z) <= smem_optin;
+}
+
+bool list_item_supported(int Z, int E, int n_rows, int max_deg) {
+    return !(Z & 1) && Z >= 2 && Z <= 2 * kThreadsP && max_deg >= 2 && max_deg <= kMaxDeg &&
+           E <= kMaxEdgesP && n_rows <= kMaxRowsP;
 }
 
 ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream) {
@@ -264,15 +345,7 @@ ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stre
     pp.H = H;
     // graph tables travel as kernel parameters (row pointers, per-edge gather metadata)
     for (int r = 0; r <= p.n_rows; ++r) pp.row[r] = p.h_row_ptr[r];
-    for (int e = 0; e < p.E; ++e) {
-        const uint32_t ed = p.h_edges[e];
-        const int c = (int)(ed >> 16), sh = (int)(ed & 0xffffu);
-        const int q = sh >= H ? 1 : 0, u = sh - q * H;
-        pp.meta[e].base_nw = c * H + u;
-        pp.meta[e].thresh = H - u;
-        pp.meta[e].sel_nw = q ? 0x1032u : 0x3210u;
-        pp.meta[e].sel_w = q ? 0x3210u : 0x1032u;
-    }
+    for (int e = 0; e < p.E; ++e) pp.meta[e] = make_meta(p.h_edges[e], H);
     const size_t smem = rowpair_smem_bytes(p.E, p.n_rows, p.n_cols, p.Z);
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
@@ -281,7 +354,6 @@ ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stre
                              (int)smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     const int threads = ((H + 31) / 32) * 32;
-    if (threads > 256) return LDPC_ERR_UNSUPPORTED;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowpair_kernel, threads, smem) !=
             cudaSuccess ||
@@ -293,6 +365,33 @@ ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stre
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
     return LDPC_OK;
+}
+
+ldpc_status launch_list(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
+                        int early_stop, cudaStream_t stream) {
+    int dev = 0, n_sm = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem > (size_t)optin) return LDPC_ERR_UNSUPPORTED;
+    if (cudaFuncSetAttribute(list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, list_kernel, kThreadsP, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return LDPC_ERR_UNSUPPORTED;
+    int grid = n_sm * per_sm;
+    if (grid > n_items) grid = n_items;
+    list_kernel<<<grid, kThreadsP, smem, stream>>>(d_items, n_items, d_counter, early_stop);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+size_t list_item_smem_bytes(int E, int n_rows, int n_cols, int Z) {
+    return rowpair_smem_bytes(E, n_rows, n_cols, Z);
 }
 
 }  // namespace ldpc

@@ -1,10 +1,15 @@
 // C-ABI entry points: graph construction (paper Sec. II code model) and the decode calls
 // (Sec. III layered min-sum over a batch, Sec. IV).  Host-side validation only; all
 // decoding work runs in the kernels of decode_layered.cu.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "ldpc_internal.h"
 
@@ -12,6 +17,18 @@ namespace ldpc {
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Per-(device, stream) workspace of the work-list decode: device work table + counter, and
+// a pinned host staging copy of the table guarded by an event.
+struct ListWorkspace {
+    ListItem *d_items = nullptr;
+    int *d_counter = nullptr;
+    ListItem *h_items = nullptr;
+    size_t cap = 0;
+    cudaEvent_t copied = nullptr;
+};
+static std::mutex g_ws_mu;
+static std::map<std::pair<int, cudaStream_t>, ListWorkspace> g_ws;
 
 }  // namespace ldpc
 
@@ -274,6 +291,99 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
         cudaStreamSynchronize(s) != cudaSuccess)
         return LDPC_ERR_CUDA;
     return LDPC_OK;
+}
+
+ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stream_t stream,
+                             const ldpc_decode_opts *opts) {
+    if (n_items < 0 || (n_items > 0 && !items)) return LDPC_ERR_INVALID_ARG;
+    ldpc_decode_opts o;
+    if (opts)
+        o = *opts;
+    else
+        ldpc_decode_opts_default(&o);
+    if (o.llr_type != LDPC_LLR_INT8 || o.algo != LDPC_OFFSET || o.offset_q != 1 ||
+        o.punct_cols != 2 || o.cluster_size != 1)
+        return LDPC_ERR_UNSUPPORTED;
+    if (n_items == 0) return LDPC_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    std::vector<std::pair<double, ldpc::ListItem>> v;
+    v.reserve((size_t)n_items);
+    size_t smem = 0;
+    for (int k = 0; k < n_items; ++k) {
+        const ldpc_work_item &w = items[k];
+        if (!w.graph || !w.llr || !w.hard_bits || !w.iters) return LDPC_ERR_INVALID_ARG;
+        Graph *g = reinterpret_cast<Graph *>(w.graph);
+        if (g->device != dev) return LDPC_ERR_INVALID_ARG;
+        const int n_rows = w.n_rows == 0 ? g->M_bg : w.n_rows;
+        if (n_rows < 1 || n_rows > g->M_bg || w.max_iter < 1 || w.max_iter > ldpc::kMaxIter)
+            return LDPC_ERR_INVALID_ARG;
+        const int n_cols = g->K_b + n_rows;
+        if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
+        const int n_tx = w.n_tx == 0 ? (n_cols - 2) * g->Z : w.n_tx;
+        if (n_tx < 0 || 2 * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+        const int E = g->row_ptr[n_rows];
+        if (g->min_deg_upto[n_rows] < 2 ||
+            !ldpc::list_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows]))
+            return LDPC_ERR_UNSUPPORTED;
+        ldpc::ListItem it;
+        it.edges = g->d_edges;
+        it.row_ptr = g->d_row_ptr;
+        it.llr = static_cast<const int8_t *>(w.llr);
+        it.bits = w.hard_bits;
+        it.iters = w.iters;
+        it.Z = g->Z;
+        it.K_b = g->K_b;
+        it.n_rows = n_rows;
+        it.n_cols = n_cols;
+        it.E = E;
+        it.n_tx = n_tx;
+        it.punct = 2;
+        it.max_iter = w.max_iter;
+        smem = std::max(smem, ldpc::list_item_smem_bytes(E, n_rows, n_cols, g->Z));
+        v.emplace_back((double)E * g->Z * w.max_iter, it);
+    }
+    // largest items first: the dynamic work counter then balances the tail
+    std::stable_sort(v.begin(), v.end(),
+                     [](const auto &a, const auto &b) { return a.first > b.first; });
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(ldpc::g_ws_mu);
+    ldpc::ListWorkspace &ws = ldpc::g_ws[std::make_pair(dev, s)];
+    if (ws.cap < (size_t)n_items) {
+        if (ws.copied) cudaEventSynchronize(ws.copied);
+        cudaFree(ws.d_items);
+        cudaFreeHost(ws.h_items);
+        ws.d_items = nullptr;
+        ws.h_items = nullptr;
+        ws.cap = 0;
+        size_t cap = 256;
+        while (cap < (size_t)n_items) cap *= 2;
+        if (cudaMalloc(&ws.d_items, cap * sizeof(ldpc::ListItem)) != cudaSuccess ||
+            cudaMallocHost(&ws.h_items, cap * sizeof(ldpc::ListItem)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(ws.d_items);
+            cudaFreeHost(ws.h_items);
+            ws.d_items = nullptr;
+            ws.h_items = nullptr;
+            return LDPC_ERR_OUT_OF_MEMORY;
+        }
+        ws.cap = cap;
+    }
+    if (!ws.d_counter && cudaMalloc(&ws.d_counter, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return LDPC_ERR_OUT_OF_MEMORY;
+    }
+    if (!ws.copied && cudaEventCreateWithFlags(&ws.copied, cudaEventDisableTiming) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    // the pinned staging copy may still feed the previous call's upload
+    if (cudaEventSynchronize(ws.copied) != cudaSuccess) return LDPC_ERR_CUDA;
+    for (int k = 0; k < n_items; ++k) ws.h_items[k] = v[(size_t)k].second;
+    if (cudaMemcpyAsync(ws.d_items, ws.h_items, (size_t)n_items * sizeof(ldpc::ListItem),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(ws.copied, s) != cudaSuccess ||
+        cudaMemsetAsync(ws.d_counter, 0, sizeof(int), s) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    return ldpc::launch_list(ws.d_items, n_items, ws.d_counter, smem, o.early_stop ? 1 : 0, s);
 }
 
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t h, ldpc_stream_t stream) {

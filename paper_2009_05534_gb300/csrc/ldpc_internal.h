@@ -55,6 +55,17 @@ struct DecodeParams {
     int *status;              // device status word
 };
 
+// One codeword of a work list (device side; built by ldpc_decode_list).
+struct ListItem {
+    const uint32_t *edges;    // graph edge table
+    const int *row_ptr;       // graph row pointers
+    const int8_t *llr;        // [n_tx]
+    uint8_t *bits;            // [ceil(K/8)]
+    int32_t *iters;           // [1]
+    int Z, K_b, n_rows, n_cols;
+    int E, n_tx, punct, max_iter;
+};
+
 // Launch entry for the layered decoder (decode_layered.cu).  Returns LDPC_OK or an error
 // found while configuring the launch.
 ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t stream);
@@ -67,6 +78,13 @@ ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream);
 // (decode_rowpair.cu).
 bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream);
+
+// Work-list decode (decode_rowpair.cu): items are taken dynamically through *d_counter,
+// which must be zero at launch.
+bool list_item_supported(int Z, int E, int n_rows, int max_deg);
+size_t list_item_smem_bytes(int E, int n_rows, int n_cols, int Z);
+ldpc_status launch_list(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
+                        int early_stop, cudaStream_t stream);
 
 void count_launch();
 

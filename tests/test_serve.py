@@ -1,0 +1,115 @@
+"""Slot scheduler: FIFO admission by memory, continuous batching, latency bookkeeping
+(CPU, fake backend), and on the GPU: each result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+from paper_2009_05534_gb300.serve import SlotScheduler, latency_stats
+
+
+class FakeBackend:
+    """Each batch completes `delay` slots after its launch (device time = delay slots)."""
+
+    def __init__(self, n_buffers, delay=2, slot_us=500.0):
+        self.n, self.delay, self.now, self.slot_us = n_buffers, delay, 0, slot_us
+        self.launched = []
+
+    def capacity(self):
+        return self.n
+
+    def launch(self, slot, ids, outs):
+        self.launched.append((slot, ids.tolist(), outs.tolist()))
+        return slot + self.delay
+
+    def done(self, handle):
+        return self.now >= handle
+
+    def wait(self, handle):
+        self.now = max(self.now, handle)
+
+    def finish(self, handle, ids, outs):
+        return self.delay * self.slot_us
+
+
+def test_fifo_admission_by_memory():
+    be = FakeBackend(n_buffers=3, delay=2)
+    sch = SlotScheduler(be, slot_us=500.0)
+    sch.submit(7)
+    for s in range(12):
+        be.now = s
+        sch.step()
+    sch.drain()
+    # slot 0 admits the first 3; buffers return when the batch completes (2 slots later)
+    assert be.launched[0][:2] == (0, [0, 1, 2])
+    order = [rid for _, ids, _ in be.launched for rid in ids]
+    assert order == list(range(7))                     # first come, first served
+    assert all(len(ids) <= 3 for _, ids, _ in be.launched)
+    # a buffer is never handed out twice while in use
+    live = {}
+    for slot, ids, outs in be.launched:
+        for o in outs:
+            assert live.get(o, -10) + 2 <= slot
+            live[o] = slot
+    lat = sch.completed_latencies()
+    assert lat.size == 7 and lat.min() == 1000.0 and lat.max() > 1000.0
+
+
+def test_continuous_batching_overlaps_slots():
+    be = FakeBackend(n_buffers=100, delay=3)
+    sch = SlotScheduler(be, slot_us=500.0)
+    for s in range(6):
+        be.now = s
+        sch.submit(4)
+        sch.step()
+    # new work was launched every slot while earlier batches were still in flight
+    assert [slot for slot, _, _ in be.launched] == list(range(6))
+    assert len(sch.in_flight) >= 2
+    sch.drain()
+    st = latency_stats(sch.completed_latencies())
+    assert st["n"] == 24 and st["p99_us"] == 1500.0
+
+
+@pytest.mark.gpu
+def test_results_same_alone_and_in_mix():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from fractions import Fraction
+
+    from paper_2009_05534_gb300 import build
+    build.build()
+    import paper_2009_05534_gb300 as ldpc
+    from paper_2009_05534_gb300.serve import GpuBackend
+    from synth import make_workload
+    rng = np.random.default_rng(3)
+    graphs, llrs, alone = {}, [], []
+    n = 60
+    table = np.zeros(n, dtype=ldpc.work_item_dtype)
+    ks = np.zeros(n, np.int64)
+    for i in range(n):
+        kind = "BG1" if rng.integers(2) else "BG2"
+        Z = int(rng.choice([32, 64, 96, 128, 192, 256, 384]))
+        rate = Fraction(str(rng.choice(["1/3", "1/2", "2/3", "5/6"])))
+        wl = make_workload(kind, Z, 1, float(rng.uniform(0.5, 4.0)), rate=rate, seed=500 + i)
+        if (kind, Z) not in graphs:
+            graphs[(kind, Z)] = ldpc.Graph(wl.base, wl.K_b, Z)
+        g = graphs[(kind, Z)]
+        llr = torch.from_numpy(wl.llr_int8()[0]).cuda()
+        llrs.append(llr)
+        table[i] = (g.handle.value, llr.data_ptr(), 0, 0, wl.n_rows, wl.n_tx, 8)
+        ks[i] = wl.K
+        b, it = ldpc.decode(g, llr[None, :], 8, n_rows=wl.n_rows, n_tx=wl.n_tx)
+        torch.cuda.synchronize()
+        alone.append((b.cpu().numpy()[0], int(it.item())))
+    kmax = max(g.K for g in graphs.values())
+    be = GpuBackend(table, ks, n_buffers=16, kmax=kmax, n_streams=3, keep_results=True)
+    sch = SlotScheduler(be, slot_us=500.0)
+    for s in range(0, n, 7):                 # 7 arrivals per slot, only 16 buffers
+        sch.submit(min(7, n - s))
+        sch.step()
+    sch.drain()
+    assert len(be.results) == n
+    for i, (b, it) in be.results.items():
+        assert np.array_equal(b, alone[i][0]) and it == alone[i][1]
+    assert (sch.completed_latencies() > 0).all()
+    for g in graphs.values():
+        g.close()
