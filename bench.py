@@ -194,7 +194,7 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
             for rate in SERVE_RATES:
                 for m, (mod, eb) in enumerate(SERVE_MODS):
                     wl = make_workload(kind, Zs, 2, eb, rate=Fraction(rate), modulation=mod,
-                                       seed=seed * 1000 + len(rows))
+                                       seed=seed * 1000 + len(rows), graph_seed=0)
                     if (kind, Zs) not in graphs:
                         graphs[(kind, Zs)] = ldpc.Graph(wl.base, wl.K_b, Zs)
                     q = torch.from_numpy(wl.llr_int8()).cuda()
@@ -213,9 +213,9 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
     be = GpuBackend(table, kreq, n_buffers=4096, kmax=kmax, n_streams=4, early_stop=True)
     sch = SlotScheduler(be, slot_us=500.0, max_requests=total + 1)
     # warm-up: a few slots outside the measurement
-    warm = SlotScheduler(GpuBackend(pool, ks, n_buffers=1024, kmax=kmax), slot_us=500.0,
-                         max_requests=4096)
-    run_paced(warm, [min(len(pool), 512)] * 3)
+    warm = SlotScheduler(GpuBackend(np.tile(pool, 4), np.tile(ks, 4), n_buffers=1024,
+                                    kmax=kmax), slot_us=500.0, max_requests=4 * len(pool) + 1)
+    run_paced(warm, [len(pool)] * 4)
     torch.cuda.synchronize()
     wall = run_paced(sch, counts.tolist(), 500.0)
     st = latency_stats(sch.completed_latencies())

@@ -61,6 +61,9 @@ def lib():
             L.oracle_syndrome_bits.restype = i
             L.oracle_edge_count.argtypes = [P, i, i, i, i, i]
             L.oracle_edge_count.restype = i
+            L.oracle_learned_grad.argtypes = [P, i, i, i, i, i, i, i, P, i, P, P, i, i,
+                                              ctypes.c_double, P, P, P, P]
+            L.oracle_learned_grad.restype = i
             L.oracle_round_half.argtypes = [ctypes.c_double]
             L.oracle_round_half.restype = ctypes.c_float
             _lib = L
@@ -177,6 +180,32 @@ def syndrome_weight(base, K_b, Z, n_rows, bits) -> int:
     x = np.ascontiguousarray(bits, dtype=np.uint8)
     return int(lib().oracle_syndrome_bits(_ptr(b), b.shape[0], b.shape[1], K_b, Z, n_rows,
                                           _ptr(x)))
+
+
+def learned_grad(base, K_b, Z, n_rows, llr, params, codewords, *, punct=2, want_post=False,
+                 want_grad_llr=False, scale=None):
+    """Loss (mean BCE of sigma(-L) against the codeword bits over batch x used bits) and its
+    gradient with respect to the learned (beta, gamma) table [T][n_rows][2] (and optionally
+    the channel LLRs), by reverse mode through the unrolled layered decoder."""
+    b = np.ascontiguousarray(base, dtype=np.int16)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    T = prm.shape[0]
+    B, n_tx = llr.shape
+    N = (K_b + n_rows) * Z
+    cw = np.ascontiguousarray(codewords[:, :N], dtype=np.uint8)
+    if scale is None:
+        scale = 1.0 / (B * N)
+    gp = np.zeros(prm.shape, np.float64)
+    gl = np.zeros((B, n_tx), np.float64) if want_grad_llr else None
+    post = np.zeros((B, N), np.float32) if want_post else None
+    loss = ctypes.c_double(0.0)
+    st = lib().oracle_learned_grad(_ptr(b), b.shape[0], b.shape[1], K_b, Z, n_rows, punct, n_tx,
+                                   _ptr(prm), T, _ptr(llr), _ptr(cw), 0, B, float(scale),
+                                   _ptr(gp), _ptr(gl), _ptr(post), ctypes.byref(loss))
+    if st != 0:
+        raise ValueError(f"oracle_learned_grad failed with status {st}")
+    return loss.value / (B * N), gp, gl, post
 
 
 def round_half(x: float) -> float:

@@ -737,3 +737,200 @@ float oracle_round_half(double x)
 {
     return round_half(x);
 }
+
+/* ------------------------------------------------- learned min-sum: forward and gradient
+ *
+ * Learned normalised-offset min-sum (an extension of the correction factor beta of
+ * Sec. III to one (beta, gamma) pair per iteration t and base row r):
+ *     m' = beta[t][r] * max(m - gamma[t][r], 0),  fp32 forward as in decode_one_f32.
+ * Loss: mean over the batch and all used bits of the binary cross-entropy between
+ * sigma(-L_v) (probability of bit 1) and the codeword bit:  softplus(-L) + c*L.
+ * Gradient: reverse-mode through the unrolled layers.  For edge e of a check row with
+ * v = L - c_old, c_new_e = s_e * beta * max(mag_e - gamma, 0), mag_e = min over the other
+ * edges of |v| (m2 on the argmin edge, m1 elsewhere), s_e = sign product over the other
+ * edges (treated as constant); the subgradient of mag_e goes to the edge attaining it
+ * (lowest index on ties), d|v|/dv = sgn(v) with sgn(0) = +1, and d max(x, 0)/dx = [x > 0].
+ * L_new = v + c_new.  Forward values of iteration t are recomputed from a checkpoint of
+ * (L_v, c2v) taken at the start of t.  Computed in double.
+ *
+ * grad_params: [T][n_rows][2] (beta, gamma), summed over the decoded range.
+ * grad_llr (optional): [batch][n_tx].  post (optional): [batch][N] final posteriors.
+ * Returns the summed (not averaged) loss over the range in *loss_sum.
+ */
+int oracle_learned_grad(const int16_t *base, int M_bg, int N_bg, int K_b, int Z, int n_rows,
+                        int punct, int n_tx, const float *params, int T, const float *llr,
+                        const uint8_t *cw_bits, int cw_begin, int cw_end, double scale,
+                        double *grad_params, double *grad_llr, float *post, double *loss_sum)
+{
+    og_graph g;
+    int st = graph_build(base, M_bg, N_bg, K_b, Z, n_rows, &g);
+    if (st != OR_OK)
+        return st;
+    const int N = g.n_cols * Z, EZ = g.E * Z;
+    const int dmax = dec_max_degree(&g);
+    float *Lv = (float *)malloc(sizeof(float) * N);
+    float *c2v = (float *)malloc(sizeof(float) * (EZ + 1));
+    float *ckL = (float *)malloc(sizeof(float) * (size_t)N * T);
+    float *ckC = (float *)malloc(sizeof(float) * (size_t)(EZ + 1) * T);
+    float *V = (float *)malloc(sizeof(float) * (EZ + 1));       /* v of every edge, one iteration */
+    double *gL = (double *)malloc(sizeof(double) * N);
+    double *gc = (double *)malloc(sizeof(double) * (EZ + 1));
+    double *gv = (double *)malloc(sizeof(double) * (dmax + 1));
+    if (!Lv || !c2v || !ckL || !ckC || !V || !gL || !gc || !gv) {
+        free(Lv); free(c2v); free(ckL); free(ckC); free(V); free(gL); free(gc); free(gv);
+        graph_free(&g);
+        return OR_NO_MEM;
+    }
+    *loss_sum = 0.0;
+    for (int b = cw_begin; b < cw_end; ++b) {
+        /* forward with checkpoints */
+        for (int j = 0; j < N; ++j)
+            Lv[j] = 0.0f;
+        for (int j = 0; j < n_tx; ++j)
+            Lv[punct * Z + j] = llr[(size_t)b * n_tx + j];
+        for (int k = 0; k < EZ; ++k)
+            c2v[k] = 0.0f;
+        for (int t = 0; t < T; ++t) {
+            memcpy(ckL + (size_t)t * N, Lv, sizeof(float) * N);
+            memcpy(ckC + (size_t)t * EZ, c2v, sizeof(float) * EZ);
+            for (int r = 0; r < g.n_rows; ++r) {
+                const float beta = params[(t * g.n_rows + r) * 2 + 0];
+                const float gamma = params[(t * g.n_rows + r) * 2 + 1];
+                const int e0 = g.row_ptr[r], d = g.row_ptr[r + 1] - e0;
+                for (int i = 0; i < Z; ++i) {
+                    float m1 = INFINITY, m2 = INFINITY;
+                    int idx = -1, S = 0;
+                    for (int k = 0; k < d; ++k) {
+                        const float v = Lv[var_of(&g, e0 + k, i)] - c2v[(e0 + k) * Z + i];
+                        V[(e0 + k) * Z + i] = v;
+                        const float a = fabsf(v);
+                        if (a < m1) {
+                            m2 = m1;
+                            m1 = a;
+                            idx = k;
+                        } else if (a < m2) {
+                            m2 = a;
+                        }
+                        S ^= (v < 0.0f);
+                    }
+                    for (int k = 0; k < d; ++k) {
+                        const float v = V[(e0 + k) * Z + i];
+                        const float mag = (k == idx) ? m2 : m1;
+                        float tm = mag - gamma;
+                        tm = tm > 0.0f ? tm : 0.0f;
+                        const float mc = beta * tm;
+                        const float cv = (S ^ (v < 0.0f)) ? -mc : mc;
+                        c2v[(e0 + k) * Z + i] = cv;
+                        Lv[var_of(&g, e0 + k, i)] = v + cv;
+                    }
+                }
+            }
+        }
+        if (post)
+            memcpy(post + (size_t)b * N, Lv, sizeof(float) * N);
+        /* loss and its gradient with respect to the final posteriors */
+        for (int j = 0; j < N; ++j) {
+            const double L = Lv[j];
+            const double c = cw_bits[(size_t)b * N + j] & 1;
+            /* softplus(-L) + c L, computed stably */
+            const double sp = (L > 0 ? log1p(exp(-L)) : -L + log1p(exp(L)));
+            *loss_sum += sp + c * L;
+            const double sig = 1.0 / (1.0 + exp(L));      /* sigma(-L) */
+            gL[j] = scale * (c - sig);
+        }
+        for (int k = 0; k < EZ; ++k)
+            gc[k] = 0.0;
+        /* reverse sweep over iterations */
+        for (int t = T - 1; t >= 0; --t) {
+            /* recompute the forward of iteration t from its checkpoint, keeping every v */
+            memcpy(Lv, ckL + (size_t)t * N, sizeof(float) * N);
+            memcpy(c2v, ckC + (size_t)t * EZ, sizeof(float) * EZ);
+            for (int r = 0; r < g.n_rows; ++r) {
+                const float beta = params[(t * g.n_rows + r) * 2 + 0];
+                const float gamma = params[(t * g.n_rows + r) * 2 + 1];
+                const int e0 = g.row_ptr[r], d = g.row_ptr[r + 1] - e0;
+                for (int i = 0; i < Z; ++i) {
+                    float m1 = INFINITY, m2 = INFINITY;
+                    int idx = -1, S = 0;
+                    for (int k = 0; k < d; ++k) {
+                        const float v = Lv[var_of(&g, e0 + k, i)] - c2v[(e0 + k) * Z + i];
+                        V[(e0 + k) * Z + i] = v;
+                        const float a = fabsf(v);
+                        if (a < m1) {
+                            m2 = m1;
+                            m1 = a;
+                            idx = k;
+                        } else if (a < m2) {
+                            m2 = a;
+                        }
+                        S ^= (v < 0.0f);
+                    }
+                    for (int k = 0; k < d; ++k) {
+                        const float v = V[(e0 + k) * Z + i];
+                        const float mag = (k == idx) ? m2 : m1;
+                        float tm = mag - gamma;
+                        tm = tm > 0.0f ? tm : 0.0f;
+                        const float mc = beta * tm;
+                        const float cv = (S ^ (v < 0.0f)) ? -mc : mc;
+                        Lv[var_of(&g, e0 + k, i)] = v + cv;
+                        c2v[(e0 + k) * Z + i] = cv;
+                    }
+                }
+            }
+            /* backward through the layers of iteration t, last layer first */
+            for (int r = g.n_rows - 1; r >= 0; --r) {
+                const double beta = params[(t * g.n_rows + r) * 2 + 0];
+                const double gamma = params[(t * g.n_rows + r) * 2 + 1];
+                const int e0 = g.row_ptr[r], d = g.row_ptr[r + 1] - e0;
+                double gb = 0.0, gg = 0.0;
+                for (int i = 0; i < Z; ++i) {
+                    /* row quantities from the stored v */
+                    float m1 = INFINITY, m2 = INFINITY;
+                    int idx = -1, idx2 = -1, S = 0;
+                    for (int k = 0; k < d; ++k) {
+                        const float a = fabsf(V[(e0 + k) * Z + i]);
+                        if (a < m1) {
+                            m2 = m1;
+                            idx2 = idx;
+                            m1 = a;
+                            idx = k;
+                        } else if (a < m2) {
+                            m2 = a;
+                            idx2 = k;
+                        }
+                        S ^= (V[(e0 + k) * Z + i] < 0.0f);
+                    }
+                    for (int k = 0; k < d; ++k)
+                        gv[k] = gL[var_of(&g, e0 + k, i)];      /* dL_new / dv = 1 */
+                    for (int k = 0; k < d; ++k) {
+                        const float v = V[(e0 + k) * Z + i];
+                        const double s = (S ^ (v < 0.0f)) ? -1.0 : 1.0;
+                        const double mag = (k == idx) ? m2 : m1;
+                        const double gcn = gL[var_of(&g, e0 + k, i)] + gc[(e0 + k) * Z + i];
+                        const double act = mag - gamma > 0.0 ? 1.0 : 0.0;
+                        gb += gcn * s * (mag - gamma > 0.0 ? mag - gamma : 0.0);
+                        gg += -gcn * s * beta * act;
+                        const double gmag = gcn * s * beta * act;
+                        const int src = (k == idx) ? idx2 : idx;   /* edge attaining mag */
+                        if (src >= 0 && gmag != 0.0) {
+                            const float vs = V[(e0 + src) * Z + i];
+                            gv[src] += gmag * (vs < 0.0f ? -1.0 : 1.0);
+                        }
+                    }
+                    for (int k = 0; k < d; ++k) {
+                        gL[var_of(&g, e0 + k, i)] = gv[k];       /* dv / dL_old = 1 */
+                        gc[(e0 + k) * Z + i] = -gv[k];           /* dv / dc_old = -1 */
+                    }
+                }
+                grad_params[(t * g.n_rows + r) * 2 + 0] += gb;
+                grad_params[(t * g.n_rows + r) * 2 + 1] += gg;
+            }
+        }
+        if (grad_llr)
+            for (int j = 0; j < n_tx; ++j)
+                grad_llr[(size_t)b * n_tx + j] = gL[punct * Z + j];
+    }
+    free(Lv); free(c2v); free(ckL); free(ckC); free(V); free(gL); free(gc); free(gv);
+    graph_free(&g);
+    return OR_OK;
+}

@@ -34,7 +34,8 @@ def _mixed(ldpc, n, seed):
         Z = int(rng.choice(ZS))
         rate = Fraction(str(rng.choice(RATES[kind])))
         T = int(rng.choice([3, 6, 10]))
-        wl = make_workload(kind, Z, 1, float(rng.uniform(0.5, 4.0)), rate=rate, seed=seed + k)
+        wl = make_workload(kind, Z, 1, float(rng.uniform(0.5, 4.0)), rate=rate, seed=seed + k,
+                           graph_seed=0)
         key = (kind, Z)
         if key not in graphs:
             graphs[key] = ldpc.Graph(wl.base, wl.K_b, Z)
