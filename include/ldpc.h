@@ -168,6 +168,35 @@ typedef struct {
 ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stream_t stream,
                              const ldpc_decode_opts *opts);
 
+/* ---- Learned min-sum (training support) ------------------------------------------
+ * A per-(iteration, base row) extension of the min-sum correction factor of Sec. III:
+ * m' = beta[t][r] * max(m - gamma[t][r], 0), binary32 arithmetic, T iterations, no early
+ * stop.  Loss-agnostic: the forward pass returns the final posteriors, the backward pass
+ * takes dLoss/dposteriors and returns dLoss/d(beta, gamma) per codeword (and optionally
+ * dLoss/dLLR), by reverse mode through the unrolled layers with the subgradient of each
+ * min routed to the edge that attains it and signs held constant.
+ *
+ * Workspace: caller-owned device memory of ldpc_learned_workspace_floats(g, batch, T,
+ * n_rows) floats; the forward pass writes the per-iteration checkpoints there and the
+ * backward pass of the same batch reads them (and uses the rest as scratch). */
+size_t ldpc_learned_workspace_floats(ldpc_graph_t g, int batch, int T, int n_rows);
+
+/*   llr_dev      device float [batch][n_tx] channel LLRs
+ *   params_dev   device float [T][n_rows][2] (beta, gamma)
+ *   post_dev     device float [batch][(K_b + n_rows) * Z] output posteriors
+ *   n_rows       0 = all rows; n_tx: 0 = from n_rows (punct_cols = 2). */
+ldpc_status ldpc_learned_forward(ldpc_graph_t g, const float *llr_dev, int batch, int T,
+                                 int n_rows, int n_tx, const float *params_dev,
+                                 ldpc_stream_t stream, float *post_dev, float *workspace_dev);
+
+/*   grad_post_dev    device float [batch][(K_b + n_rows) * Z]: dLoss/dposteriors
+ *   grad_params_dev  device float [batch][T][n_rows][2] output (per codeword)
+ *   grad_llr_dev     device float [batch][n_tx] output, or NULL */
+ldpc_status ldpc_learned_backward(ldpc_graph_t g, const float *grad_post_dev, int batch, int T,
+                                  int n_rows, int n_tx, const float *params_dev,
+                                  ldpc_stream_t stream, float *workspace_dev,
+                                  float *grad_params_dev, float *grad_llr_dev);
+
 /* Wait for the graph's outstanding work on `stream` and return (then clear) the device
  * status word: LDPC_OK, or the first error a kernel reported (e.g. LDPC_ERR_TIMEOUT). */
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t g, ldpc_stream_t stream);

@@ -386,6 +386,70 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
     return ldpc::launch_list(ws.d_items, n_items, ws.d_counter, smem, o.early_stop ? 1 : 0, s);
 }
 
+static ldpc_status learned_common(ldpc_graph_t h, int batch, int T, int n_rows_in, int n_tx_in,
+                                  ldpc::DecodeParams *p) {
+    if (!h || batch < 0 || T < 1 || T > ldpc::kMaxIter) return LDPC_ERR_INVALID_ARG;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    const int n_rows = n_rows_in == 0 ? g->M_bg : n_rows_in;
+    if (n_rows < 1 || n_rows > g->M_bg) return LDPC_ERR_INVALID_ARG;
+    const int n_cols = g->K_b + n_rows;
+    if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
+    if (g->min_deg_upto[n_rows] < 2) return LDPC_ERR_UNSUPPORTED;
+    const int n_tx = n_tx_in == 0 ? (n_cols - 2) * g->Z : n_tx_in;
+    if (n_tx < 0 || 2 * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != g->device) return LDPC_ERR_INVALID_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->edges = g->d_edges;
+    p->row_ptr = g->d_row_ptr;
+    p->h_edges = g->h_edges;
+    p->h_row_ptr = g->row_ptr;
+    p->n_rows = n_rows;
+    p->E = g->row_ptr[n_rows];
+    p->Z = g->Z;
+    p->n_cols = n_cols;
+    p->K_b = g->K_b;
+    p->max_deg = g->max_deg_upto[n_rows];
+    p->punct = 2;
+    p->n_tx = n_tx;
+    p->max_iter = T;
+    p->batch = batch;
+    p->algo = LDPC_LEARNED;
+    p->status = g->d_status;
+    return LDPC_OK;
+}
+
+size_t ldpc_learned_workspace_floats(ldpc_graph_t h, int batch, int T, int n_rows) {
+    ldpc::DecodeParams p;
+    if (learned_common(h, batch, T, n_rows, 0, &p) != LDPC_OK) return 0;
+    return (size_t)batch * ldpc::learned_ws_floats_per_cw(p.n_cols * p.Z, p.E * p.Z, T);
+}
+
+ldpc_status ldpc_learned_forward(ldpc_graph_t h, const float *llr, int batch, int T, int n_rows,
+                                 int n_tx, const float *params, ldpc_stream_t stream, float *post,
+                                 float *ws) {
+    ldpc::DecodeParams p;
+    ldpc_status st = learned_common(h, batch, T, n_rows, n_tx, &p);
+    if (st != LDPC_OK) return st;
+    if (batch == 0) return LDPC_OK;
+    if (!llr || !params || !post || !ws) return LDPC_ERR_INVALID_ARG;
+    return ldpc::launch_learned(p, T, params, llr, post, nullptr, nullptr, nullptr, ws, false,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+ldpc_status ldpc_learned_backward(ldpc_graph_t h, const float *grad_post, int batch, int T,
+                                  int n_rows, int n_tx, const float *params, ldpc_stream_t stream,
+                                  float *ws, float *grad_params, float *grad_llr) {
+    ldpc::DecodeParams p;
+    ldpc_status st = learned_common(h, batch, T, n_rows, n_tx, &p);
+    if (st != LDPC_OK) return st;
+    if (batch == 0) return LDPC_OK;
+    if (!grad_post || !params || !ws || !grad_params) return LDPC_ERR_INVALID_ARG;
+    return ldpc::launch_learned(p, T, params, nullptr, nullptr, grad_post, grad_params, grad_llr,
+                                ws, true, reinterpret_cast<cudaStream_t>(stream));
+}
+
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t h, ldpc_stream_t stream) {
     if (!h) return LDPC_ERR_INVALID_ARG;
     Graph *g = reinterpret_cast<Graph *>(h);
