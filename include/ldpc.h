@@ -168,6 +168,25 @@ typedef struct {
 ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stream_t stream,
                              const ldpc_decode_opts *opts);
 
+/* Same as ldpc_decode_list, for callers that cannot allocate device memory (code running
+ * inside another framework's memory pool, behind a fixed memory map, or on a path where a
+ * cudaMalloc would synchronise the device).  The paper has no counterpart: this is a
+ * deployment variant of the work-list decode.
+ *   - Allocates nothing: no cudaMalloc / cudaFree / pinned host memory / heap.  The work
+ *     table and the work counter live in a static device array inside the library, sized
+ *     for at most 2048 items; every GPU that loads the library keeps it until exit.
+ *     Longer lists return LDPC_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU (different
+ *     streams, or no ordering between them) race and may decode the wrong items.  The
+ *     counter is cleared by each call.
+ *   - The table is uploaded from pageable memory, so the call may wait for the stream's
+ *     earlier work before it returns.
+ * Outputs and supported shapes are those of ldpc_decode_list. */
+ldpc_status ldpc_decode_list_noalloc(const ldpc_work_item *items, int n_items,
+                                     ldpc_stream_t stream, const ldpc_decode_opts *opts);
+
 /* ---- Learned min-sum (training support) ------------------------------------------
  * A per-(iteration, base row) extension of the min-sum correction factor of Sec. III:
  * m' = beta[t][r] * max(m - gamma[t][r], 0), binary32 arithmetic, T iterations, no early

@@ -51,7 +51,7 @@ _lock = threading.Lock()
 ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_destroy",
                "ldpc_graph_edges", "ldpc_graph_vars", "ldpc_decode", "ldpc_decode_debug",
                "ldpc_graph_sync_status", "ldpc_status_string", "ldpc_launch_count",
-               "ldpc_decode_host", "ldpc_decode_list")
+               "ldpc_decode_host", "ldpc_decode_list", "ldpc_decode_list_noalloc")
 
 
 def lib():
@@ -84,6 +84,9 @@ def lib():
             L.ldpc_decode_list.argtypes = [ctypes.POINTER(WorkItem), i, P,
                                            ctypes.POINTER(DecodeOpts)]
             L.ldpc_decode_list.restype = i
+            L.ldpc_decode_list_noalloc.argtypes = [ctypes.POINTER(WorkItem), i, P,
+                                                   ctypes.POINTER(DecodeOpts)]
+            L.ldpc_decode_list_noalloc.restype = i
             L.ldpc_graph_sync_status.argtypes = [P, P]
             L.ldpc_graph_sync_status.restype = i
             L.ldpc_status_string.argtypes = [i]
@@ -276,6 +279,20 @@ def decode_list(items, *, stream=None, early_stop=True):
         arr[k] = (g.handle.value, llr.data_ptr(), bits.data_ptr(), it.data_ptr(), int(n_rows),
                   int(n_tx), int(max_iter))
     decode_list_array(arr, stream=stream, early_stop=early_stop)
+
+
+def decode_list_noalloc(items: np.ndarray, *, stream=None, early_stop=True):
+    """ldpc_decode_list_noalloc on a numpy record array of ``work_item_dtype``.
+
+    For callers that cannot allocate device memory: the library allocates nothing on this
+    path; the work table (at most 2048 items) and the work counter sit in one static device
+    array shared by every call, so calls must not overlap on the GPU.  The first call on a
+    device looks the array up and should come before any stream capture."""
+    arr = np.ascontiguousarray(items, dtype=work_item_dtype)
+    o = make_opts(LLR_INT8, early_stop=early_stop)
+    _check(lib().ldpc_decode_list_noalloc(arr.ctypes.data_as(ctypes.POINTER(WorkItem)), len(arr),
+                                          _stream_ptr(stream), ctypes.byref(o)),
+           "ldpc_decode_list_noalloc")
 
 
 def unpack_bits(packed: np.ndarray, K: int) -> np.ndarray:

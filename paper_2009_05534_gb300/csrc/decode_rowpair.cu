@@ -26,6 +26,8 @@
 //   m1' elsewhere (ties give m2 = m1), so no argmin index is needed on the forward pass.
 // * One thread owns one row pair of every layer; the per-edge gather metadata sits in
 //   shared memory and is read with one broadcast 16-byte load per edge.
+#include <mutex>
+
 #include "f16x2.h"
 #include "ldpc_internal.h"
 
@@ -392,6 +394,54 @@ ldpc_status launch_list(const ListItem *d_items, int n_items, int *d_counter, si
 
 size_t list_item_smem_bytes(int E, int n_rows, int n_cols, int Z) {
     return rowpair_smem_bytes(E, n_rows, n_cols, Z);
+}
+
+// ------------------------------------------------- work list without allocation
+//
+// Some callers cannot allocate device memory: code that runs inside another framework's
+// memory pool, under a driver or RTOS layer with a fixed memory map, or on a path where a
+// cudaMalloc would synchronise the device.  For them the work table and the work counter
+// of the work-list decode live in this file-scope array, which every GPU that loads the
+// library keeps until exit.  Host code only ever sees the array's host-side stand-in, so
+// its device address is looked up once per device with cudaGetSymbolAddress.
+
+namespace {
+struct NoAllocScratch {
+    ListItem items[kNoAllocMaxItems];
+    int counter;
+};
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+std::mutex g_noalloc_mu;                         // guards the host-side staging below
+NoAllocScratch *g_noalloc_dev[64] = {};          // device address, per device ordinal
+ListItem g_noalloc_host[kNoAllocMaxItems];        // host staging of the sorted table
+}  // namespace
+
+ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t smem,
+                                int early_stop, cudaStream_t stream) {
+    if (n_items < 0 || n_items > kNoAllocMaxItems) return LDPC_ERR_INVALID_ARG;
+    if (n_items == 0) return LDPC_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LDPC_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_dev[dev]) {
+        // set-up: once per device, with that device current
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return LDPC_ERR_CUDA;
+        }
+        g_noalloc_dev[dev] = static_cast<NoAllocScratch *>(ptr);
+    }
+    NoAllocScratch *d = g_noalloc_dev[dev];
+    for (int k = 0; k < n_items; ++k) g_noalloc_host[k] = h_items[k];
+    // pageable source: the copy is staged before cudaMemcpyAsync returns, so the static
+    // staging array is free again for the next call
+    if (cudaMemcpyAsync(d->items, g_noalloc_host, (size_t)n_items * sizeof(ListItem),
+                        cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemsetAsync(&d->counter, 0, sizeof(int), stream) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    return launch_list(d->items, n_items, &d->counter, smem, early_stop, stream);
 }
 
 }  // namespace ldpc

@@ -386,6 +386,86 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
     return ldpc::launch_list(ws.d_items, n_items, ws.d_counter, smem, o.early_stop ? 1 : 0, s);
 }
 
+// Validation for the allocation-free work list: writes the device items into the caller's
+// fixed arrays and the launch order (largest work first) into order[0..n).
+static ldpc_status prepare_list_noalloc(const ldpc_work_item *items, int n_items,
+                                const ldpc_decode_opts *opts, ldpc::ListItem *out,
+                                int *order, double *work, size_t *smem_out, int *early_stop) {
+    ldpc_decode_opts o;
+    if (opts)
+        o = *opts;
+    else
+        ldpc_decode_opts_default(&o);
+    if (o.llr_type != LDPC_LLR_INT8 || o.algo != LDPC_OFFSET || o.offset_q != 1 ||
+        o.punct_cols != 2 || o.cluster_size != 1)
+        return LDPC_ERR_UNSUPPORTED;
+    *early_stop = o.early_stop ? 1 : 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    size_t smem = 0;
+    for (int k = 0; k < n_items; ++k) {
+        const ldpc_work_item &w = items[k];
+        if (!w.graph || !w.llr || !w.hard_bits || !w.iters) return LDPC_ERR_INVALID_ARG;
+        Graph *g = reinterpret_cast<Graph *>(w.graph);
+        if (g->device != dev) return LDPC_ERR_INVALID_ARG;
+        const int n_rows = w.n_rows == 0 ? g->M_bg : w.n_rows;
+        if (n_rows < 1 || n_rows > g->M_bg || w.max_iter < 1 || w.max_iter > ldpc::kMaxIter)
+            return LDPC_ERR_INVALID_ARG;
+        const int n_cols = g->K_b + n_rows;
+        if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
+        const int n_tx = w.n_tx == 0 ? (n_cols - 2) * g->Z : w.n_tx;
+        if (n_tx < 0 || 2 * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+        const int E = g->row_ptr[n_rows];
+        if (g->min_deg_upto[n_rows] < 2 ||
+            !ldpc::list_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows]))
+            return LDPC_ERR_UNSUPPORTED;
+        ldpc::ListItem &it = out[k];
+        it.edges = g->d_edges;
+        it.row_ptr = g->d_row_ptr;
+        it.llr = static_cast<const int8_t *>(w.llr);
+        it.bits = w.hard_bits;
+        it.iters = w.iters;
+        it.Z = g->Z;
+        it.K_b = g->K_b;
+        it.n_rows = n_rows;
+        it.n_cols = n_cols;
+        it.E = E;
+        it.n_tx = n_tx;
+        it.punct = 2;
+        it.max_iter = w.max_iter;
+        smem = std::max(smem, ldpc::list_item_smem_bytes(E, n_rows, n_cols, g->Z));
+        order[k] = k;
+        work[k] = (double)E * g->Z * w.max_iter;
+    }
+    // largest items first (ties keep list order): the dynamic work counter then balances
+    // the tail.  std::sort works in place, so this path allocates nothing.
+    std::sort(order, order + n_items, [work](int a, int b) {
+        return work[a] > work[b] || (work[a] == work[b] && a < b);
+    });
+    *smem_out = smem;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_decode_list_noalloc(const ldpc_work_item *items, int n_items,
+                                     ldpc_stream_t stream, const ldpc_decode_opts *opts) {
+    if (n_items < 0 || (n_items > 0 && !items)) return LDPC_ERR_INVALID_ARG;
+    if (n_items > ldpc::kNoAllocMaxItems) return LDPC_ERR_INVALID_ARG;   // beyond the array
+    if (n_items == 0) return LDPC_OK;
+    // host-side working arrays are fixed-size statics: nothing on this path allocates
+    static std::mutex mu;
+    static ldpc::ListItem raw[ldpc::kNoAllocMaxItems], sorted[ldpc::kNoAllocMaxItems];
+    static int order[ldpc::kNoAllocMaxItems];
+    static double work[ldpc::kNoAllocMaxItems];
+    std::lock_guard<std::mutex> lk(mu);
+    size_t smem = 0;
+    int early_stop = 1;
+    ldpc_status st = prepare_list_noalloc(items, n_items, opts, raw, order, work, &smem, &early_stop);
+    if (st != LDPC_OK) return st;
+    for (int k = 0; k < n_items; ++k) sorted[k] = raw[order[k]];
+    return ldpc::launch_list_noalloc(sorted, n_items, smem, early_stop,
+                                     reinterpret_cast<cudaStream_t>(stream));
+}
+
 static ldpc_status learned_common(ldpc_graph_t h, int batch, int T, int n_rows_in, int n_tx_in,
                                   ldpc::DecodeParams *p) {
     if (!h || batch < 0 || T < 1 || T > ldpc::kMaxIter) return LDPC_ERR_INVALID_ARG;

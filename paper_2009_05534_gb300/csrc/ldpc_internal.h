@@ -92,6 +92,12 @@ size_t list_item_smem_bytes(int E, int n_rows, int n_cols, int Z);
 ldpc_status launch_list(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
                         int early_stop, cudaStream_t stream);
 
+// Work-list decode whose work table and counter sit in a static device array
+// (decode_rowpair.cu); h_items is sorted host-side already.
+constexpr int kNoAllocMaxItems = 2048;
+ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t smem,
+                                int early_stop, cudaStream_t stream);
+
 void count_launch();
 
 }  // namespace ldpc
