@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-slots", type=int, default=2000,
                     help="slots of the mixed-traffic serving measurement (0 = skip)")
+    ap.add_argument("--no-high-load", dest="high_load", action="store_false",
+                    help="skip the rate-8/9 QAM int8-vs-binary16 measurement")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip the learned-vs-plain BLER and throughput measurement")
     return ap.parse_args()
 
 
@@ -229,6 +233,135 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
             "traffic": "BG1|BG2 x Z{32..384} x R{1/3..8/9} x QPSK/16QAM/64QAM int8"}
 
 
+# ------------------------------------------------------------------- high load (R = 8/9)
+
+# Eb/N0 per modulation where the int8 decoder's BLER at a 10-iteration cap sits near 1e-2
+# on the BG1-shaped graph at rate 8/9 (oracle sweep, 200 codewords per point)
+HIGH_LOAD = (("16QAM", 7.75), ("64QAM", 11.75))
+
+
+def _timed(fn, reps: int, stream):
+    import torch
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for k in range(reps):
+        fn(k)
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / 1e3 / reps
+
+
+def high_load_measure(batch: int = 8192, caps=(5, 10, 20), reps: int = 5, seed: int = 2):
+    """BG1-shaped Z=384 at rate 8/9 (5 rows), 16QAM / 64QAM max-log LLRs, batch 8192,
+    iteration caps 5/10/20 with early stop: int8 (offset 1) and binary16 (normalised 0.75)
+    message storage side by side.  Inputs rotate over device copies larger than L2."""
+    from fractions import Fraction
+
+    import torch
+
+    import paper_2009_05534_gb300 as ldpc
+    from synth import make_workload
+    stream = torch.cuda.Stream()
+    out = []
+    for mod, eb in HIGH_LOAD:
+        wl = make_workload("BG1", 384, batch, eb, rate=Fraction(8, 9), modulation=mod,
+                           seed=seed, graph_seed=0)
+        g = ldpc.Graph(wl.base, wl.K_b, 384)
+        info = torch.from_numpy(wl.info).cuda()
+        for dtype, host, kw in (("int8", wl.llr_int8(), dict(algo=ldpc.OFFSET)),
+                                ("fp16", wl.llr_fp16(),
+                                 dict(algo=ldpc.NORMALISED, alpha=0.75))):
+            n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
+            with torch.cuda.stream(stream):
+                bufs = [torch.from_numpy(host).cuda() for _ in range(n_copies)]
+            torch.cuda.synchronize()
+            for T in caps:
+                bits = iters = None
+
+                def run(k):
+                    nonlocal bits, iters
+                    bits, iters = ldpc.decode(g, bufs[k % n_copies], T, n_rows=wl.n_rows,
+                                              n_tx=wl.n_tx, early_stop=True, stream=stream,
+                                              **kw)
+
+                for k in range(2):
+                    run(k)
+                sec = _timed(run, reps, stream)
+                got = ldpc.unpack_bits(bits.cpu().numpy(), wl.K)
+                bler = float((torch.from_numpy(got).cuda() != info).any(1).float().mean())
+                out.append({"modulation": mod, "ebn0_db": eb, "max_iter": T, "dtype": dtype,
+                            "gbps": batch * wl.K / sec / 1e9, "bler": bler,
+                            "mean_iterations": float(iters.float().mean())})
+            del bufs
+        g.close()
+    return {"workload": "BG1-shaped Z=384 K=8448 R=8/9 (5 rows, N_tx=9504), batch "
+                        f"{batch}, early stop, inputs rotate over copies > L2",
+            "points": out}
+
+
+# -------------------------------------------------------- learned vs plain (BG2, Z = 128)
+
+LEARNED_TABLE = "learned_bg2_z128_t10.json"
+
+
+def learned_measure(n_cw: int = 8192, grid=(3.0, 3.25, 3.5, 3.75, 4.0, 4.25), batch: int = 8192,
+                    reps: int = 5):
+    """The trained (beta, gamma) table against plain normalised min-sum (alpha 0.75) on the
+    same fresh codewords: BLER per Eb/N0 at T = 10 (binary16 LLRs and messages), the Eb/N0
+    of BLER 1e-2 for each, and decode throughput of both at T = 10 and, with early stop,
+    at the plain decoder's BLER-1e-2 point."""
+    import torch
+
+    import paper_2009_05534_gb300 as ldpc
+    from paper_2009_05534_gb300.train_learned import (TABLE_DIR, bler_sweep, ebn0_at,
+                                                      load_table)
+    from synth import make_workload
+    path = os.path.join(TABLE_DIR, LEARNED_TABLE)
+    if not os.path.exists(path):
+        return None
+    table, meta = load_table(path)
+    T = int(meta["T"])
+    wl0 = make_workload("BG2", 128, 1, 1.0, seed=0, graph_seed=0)
+    g = ldpc.Graph(wl0.base, wl0.K_b, 128)
+    tab = torch.from_numpy(table).cuda()
+    curves = bler_sweep(g, "BG2", 128, T, {"plain": None, "learned": tab}, list(grid), n_cw,
+                        4096, seed=77_000)
+    at = {k: ebn0_at(list(grid), v, 1e-2) for k, v in curves.items()}
+    eb_op = at["plain"] if at["plain"] is not None else grid[-1]
+    stream = torch.cuda.Stream()
+    thr = {}
+    for es in (False, True):
+        wl = make_workload("BG2", 128, batch, float(eb_op), seed=78_000, graph_seed=0)
+        host = wl.llr_fp16()
+        n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
+        with torch.cuda.stream(stream):
+            bufs = [torch.from_numpy(host).cuda() for _ in range(n_copies)]
+        torch.cuda.synchronize()
+        for name, kw in (("plain", dict(algo=ldpc.NORMALISED, alpha=0.75)),
+                         ("learned", dict(algo=ldpc.LEARNED, learned=tab))):
+            iters = None
+
+            def run(k):
+                nonlocal iters
+                _, iters = ldpc.decode(g, bufs[k % n_copies], T, early_stop=es, stream=stream,
+                                       **kw)
+
+            for k in range(2):
+                run(k)
+            sec = _timed(run, reps, stream)
+            thr[f"{name}{'_early_stop' if es else ''}"] = {
+                "gbps": batch * wl.K / sec / 1e9, "mean_iterations": float(iters.float().mean())}
+        del bufs
+    g.close()
+    return {"workload": meta.get("code"), "T": T, "llr": "binary16", "eval_codewords": n_cw,
+            "ebn0_db": list(grid), "bler_plain": curves["plain"],
+            "bler_learned": curves["learned"], "ebn0_at_bler_1e-2": at,
+            "gain_db": (at["plain"] - at["learned"]) if None not in at.values() else None,
+            "throughput_ebn0_db": eb_op, "throughput": thr,
+            "training": {k: meta["training"].get(k) for k in
+                         ("codewords", "epochs", "steps", "lr", "ebn0_db", "loss")}}
+
+
 # ----------------------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -385,6 +518,8 @@ def run_ours(args):
     traffic = profiled_traffic("layered_int8_bg1_z384")
 
     serving = serving_measure(args.serve_slots) if args.serve_slots > 0 else None
+    high_load = high_load_measure() if args.high_load else None
+    learned = learned_measure() if args.learned else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -417,6 +552,8 @@ def run_ours(args):
             "e2e": {"value": e2e, "unit": "Gbit/s", "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": B * (nbytes + 4)},
             "serving": serving,
+            "high_load": high_load,
+            "learned": learned,
             "gpu_launches": launches,
             "clocks": clocks,
             "wall_s": t_wall,

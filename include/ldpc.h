@@ -216,6 +216,25 @@ ldpc_status ldpc_learned_backward(ldpc_graph_t g, const float *grad_post_dev, in
                                   ldpc_stream_t stream, float *workspace_dev,
                                   float *grad_params_dev, float *grad_llr_dev);
 
+/* Per-iteration variants, for a loss over the posteriors after every iteration.
+ *   post_iter_dev       device float [T][batch][(K_b + n_rows) * Z] output: slice t holds
+ *                       the posteriors after iteration t + 1 (slice T-1 = final posteriors)
+ *   grad_post_iter_dev  device float [T][batch][(K_b + n_rows) * Z]: dLoss/d(slice t)
+ * Other arguments, the workspace contract and the outputs are those of
+ * ldpc_learned_forward / ldpc_learned_backward.  The reverse sweep adds the adjoint of
+ * slice t when it reaches the end of iteration t + 1, so grad_params is the gradient of
+ * the loss summed over all slices.  Not in the paper (training support, like the functions
+ * above). */
+ldpc_status ldpc_learned_forward_iter(ldpc_graph_t g, const float *llr_dev, int batch, int T,
+                                      int n_rows, int n_tx, const float *params_dev,
+                                      ldpc_stream_t stream, float *post_iter_dev,
+                                      float *workspace_dev);
+ldpc_status ldpc_learned_backward_iter(ldpc_graph_t g, const float *grad_post_iter_dev,
+                                       int batch, int T, int n_rows, int n_tx,
+                                       const float *params_dev, ldpc_stream_t stream,
+                                       float *workspace_dev, float *grad_params_dev,
+                                       float *grad_llr_dev);
+
 /* Wait for the graph's outstanding work on `stream` and return (then clear) the device
  * status word: LDPC_OK, or the first error a kernel reported (e.g. LDPC_ERR_TIMEOUT). */
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t g, ldpc_stream_t stream);

@@ -62,7 +62,7 @@ def lib():
             L.oracle_edge_count.argtypes = [P, i, i, i, i, i]
             L.oracle_edge_count.restype = i
             L.oracle_learned_grad.argtypes = [P, i, i, i, i, i, i, i, P, i, P, P, i, i,
-                                              ctypes.c_double, P, P, P, P]
+                                              ctypes.c_double, P, P, P, P, P]
             L.oracle_learned_grad.restype = i
             L.oracle_round_half.argtypes = [ctypes.c_double]
             L.oracle_round_half.restype = ctypes.c_float
@@ -183,10 +183,13 @@ def syndrome_weight(base, K_b, Z, n_rows, bits) -> int:
 
 
 def learned_grad(base, K_b, Z, n_rows, llr, params, codewords, *, punct=2, want_post=False,
-                 want_grad_llr=False, scale=None):
+                 want_grad_llr=False, scale=None, iter_weights=None):
     """Loss (mean BCE of sigma(-L) against the codeword bits over batch x used bits) and its
     gradient with respect to the learned (beta, gamma) table [T][n_rows][2] (and optionally
-    the channel LLRs), by reverse mode through the unrolled layered decoder."""
+    the channel LLRs), by reverse mode through the unrolled layered decoder.
+
+    iter_weights ([T], optional): loss = sum_t w[t] * BCE(posteriors after iteration t);
+    None is the final-posterior loss."""
     b = np.ascontiguousarray(base, dtype=np.int16)
     llr = np.ascontiguousarray(llr, dtype=np.float32)
     prm = np.ascontiguousarray(params, dtype=np.float32)
@@ -200,9 +203,14 @@ def learned_grad(base, K_b, Z, n_rows, llr, params, codewords, *, punct=2, want_
     gl = np.zeros((B, n_tx), np.float64) if want_grad_llr else None
     post = np.zeros((B, N), np.float32) if want_post else None
     loss = ctypes.c_double(0.0)
+    iw = None
+    if iter_weights is not None:
+        iw = np.ascontiguousarray(iter_weights, dtype=np.float64)
+        if iw.shape != (T,):
+            raise ValueError("iter_weights needs one weight per iteration")
     st = lib().oracle_learned_grad(_ptr(b), b.shape[0], b.shape[1], K_b, Z, n_rows, punct, n_tx,
                                    _ptr(prm), T, _ptr(llr), _ptr(cw), 0, B, float(scale),
-                                   _ptr(gp), _ptr(gl), _ptr(post), ctypes.byref(loss))
+                                   _ptr(iw), _ptr(gp), _ptr(gl), _ptr(post), ctypes.byref(loss))
     if st != 0:
         raise ValueError(f"oracle_learned_grad failed with status {st}")
     return loss.value / (B * N), gp, gl, post

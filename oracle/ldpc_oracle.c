@@ -30,6 +30,7 @@
  *   - int8: L_v, v->c and c->v saturate to [-127, 127] (-128 never used).
  *   - fp16: every stored message and posterior is rounded to binary16 (round to nearest
  *     even) after each operation; the rounding is written from the IEEE 754 definition.
+ *     The correction parameters (alpha, offset, beta, gamma) are rounded to binary16 once.
  *   - stopping: after every full iteration the syndrome of the hard decisions over the
  *     used rows is computed; all zero ends decoding (no test before iteration 1).  A
  *     stopped codeword's posteriors are frozen; iterations = number executed.
@@ -223,19 +224,21 @@ static int corr_i8(const cn_corr *c, int m)
     return t > 0 ? t : 0;
 }
 
+/* binary16 path: the correction parameters are themselves binary16 values (each rounded
+ * once from its fp32 input), so every step of the check rule is one binary16 operation. */
 static float corr_f16(const cn_corr *c, float m)
 {
     switch (c->mode) {
     case OR_NORMALISED:
-        return round_half((double)c->alpha * (double)m);
+        return round_half((double)round_half(c->alpha) * (double)m);
     case OR_OFFSET: {
-        float t = round_half((double)m - (double)c->offset);
+        float t = round_half((double)m - (double)round_half(c->offset));
         return t > 0.0f ? t : 0.0f;
     }
     default: {
-        float t = round_half((double)m - (double)c->gamma);
+        float t = round_half((double)m - (double)round_half(c->gamma));
         t = t > 0.0f ? t : 0.0f;
-        return round_half((double)c->beta * (double)t);
+        return round_half((double)round_half(c->beta) * (double)t);
     }
     }
 }
@@ -753,14 +756,28 @@ float oracle_round_half(double x)
  * L_new = v + c_new.  Forward values of iteration t are recomputed from a checkpoint of
  * (L_v, c2v) taken at the start of t.  Computed in double.
  *
+ * iter_weight (optional, [T]): the loss is sum_t iter_weight[t] * (BCE of the posteriors
+ * after iteration t); NULL means the final posteriors only (weight 1 on t = T-1).  The
+ * adjoint of the posteriors after iteration t then gains that term's gradient before
+ * iteration t is undone.
+ *
  * grad_params: [T][n_rows][2] (beta, gamma), summed over the decoded range.
  * grad_llr (optional): [batch][n_tx].  post (optional): [batch][N] final posteriors.
- * Returns the summed (not averaged) loss over the range in *loss_sum.
+ * Returns the summed (not averaged) weighted loss over the range in *loss_sum.
  */
+static double bce_term(double L, double c, double *grad)
+{
+    /* softplus(-L) + c L, computed stably; d/dL = c - sigma(-L) */
+    const double sp = (L > 0 ? log1p(exp(-L)) : -L + log1p(exp(L)));
+    *grad = c - 1.0 / (1.0 + exp(L));
+    return sp + c * L;
+}
+
 int oracle_learned_grad(const int16_t *base, int M_bg, int N_bg, int K_b, int Z, int n_rows,
                         int punct, int n_tx, const float *params, int T, const float *llr,
                         const uint8_t *cw_bits, int cw_begin, int cw_end, double scale,
-                        double *grad_params, double *grad_llr, float *post, double *loss_sum)
+                        const double *iter_weight, double *grad_params, double *grad_llr,
+                        float *post, double *loss_sum)
 {
     og_graph g;
     int st = graph_build(base, M_bg, N_bg, K_b, Z, n_rows, &g);
@@ -828,20 +845,26 @@ int oracle_learned_grad(const int16_t *base, int M_bg, int N_bg, int K_b, int Z,
         }
         if (post)
             memcpy(post + (size_t)b * N, Lv, sizeof(float) * N);
-        /* loss and its gradient with respect to the final posteriors */
+        /* loss term of the final posteriors and its gradient */
+        const double w_last = iter_weight ? iter_weight[T - 1] : 1.0;
         for (int j = 0; j < N; ++j) {
-            const double L = Lv[j];
-            const double c = cw_bits[(size_t)b * N + j] & 1;
-            /* softplus(-L) + c L, computed stably */
-            const double sp = (L > 0 ? log1p(exp(-L)) : -L + log1p(exp(L)));
-            *loss_sum += sp + c * L;
-            const double sig = 1.0 / (1.0 + exp(L));      /* sigma(-L) */
-            gL[j] = scale * (c - sig);
+            double gj;
+            *loss_sum += w_last * bce_term(Lv[j], cw_bits[(size_t)b * N + j] & 1, &gj);
+            gL[j] = scale * w_last * gj;
         }
         for (int k = 0; k < EZ; ++k)
             gc[k] = 0.0;
         /* reverse sweep over iterations */
         for (int t = T - 1; t >= 0; --t) {
+            /* loss term of the posteriors after iteration t (< T-1): the checkpoint of t+1 */
+            if (iter_weight && t < T - 1 && iter_weight[t] != 0.0)
+                for (int j = 0; j < N; ++j) {
+                    double gj;
+                    *loss_sum += iter_weight[t] *
+                                 bce_term(ckL[(size_t)(t + 1) * N + j],
+                                          cw_bits[(size_t)b * N + j] & 1, &gj);
+                    gL[j] += scale * iter_weight[t] * gj;
+                }
             /* recompute the forward of iteration t from its checkpoint, keeping every v */
             memcpy(Lv, ckL + (size_t)t * N, sizeof(float) * N);
             memcpy(c2v, ckC + (size_t)t * EZ, sizeof(float) * EZ);

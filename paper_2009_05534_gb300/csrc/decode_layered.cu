@@ -269,6 +269,8 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
         return launch_tmem(p, stream);
     if (rowpair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
         return launch_rowpair(p, p.max_deg, stream);
+    if (tmem16_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
+        return launch_tmem16(p, stream);
     switch (llr_type) {
     case LDPC_LLR_INT8:
         return launch_t<ArithI8>(p, stream);

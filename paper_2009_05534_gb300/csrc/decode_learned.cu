@@ -24,6 +24,12 @@
 //     for e = argmin, lowest index on ties), signs held constant, g_v[e] += gL[var_e];
 //     then gL[var_e] = g_v[e] and G[e] = -g_v[e].
 // Parameter gradients are reduced deterministically per (codeword, t, r).
+//
+// Per-iteration outputs: the forward pass can also write the posteriors after every
+// iteration (post_iter[t][cw]), and the backward pass then takes one adjoint per iteration
+// (grad_post_iter[t][cw]); the adjoint of iteration t < T-1 is added to gL before the
+// layers of iteration t are undone, so a loss over every iteration's posteriors
+// back-propagates in one sweep.
 #include <cuda_fp16.h>
 
 #include "ldpc_internal.h"
@@ -43,6 +49,8 @@ struct LearnedParams {
     const float *grad_post;  // [batch][N]            (backward)
     float *grad_params;      // [batch][T][n_rows][2] (backward)
     float *grad_llr;         // [batch][n_tx] or null (backward)
+    float *post_iter;        // [T][batch][N] or null (forward)
+    const float *grad_post_iter;  // [T][batch][N] or null (backward, replaces grad_post)
     float *ws;               // workspace
     size_t ws_per_cw;        // floats per codeword
 };
@@ -123,8 +131,13 @@ __global__ void __launch_bounds__(512, 1) learned_fwd_kernel(LearnedParams p) {
                     fwd_row(p, s_edge, e0, d, i, beta, gamma, L, c_old, c_new, nullptr);
                 __syncthreads();
             }
+            if (p.post_iter) {
+                float *o = p.post_iter + ((size_t)t * p.batch + cw) * N;
+                for (int j = tid; j < N; j += nthr) o[j] = L[j];
+            }
         }
-        for (int j = tid; j < N; j += nthr) p.post[(size_t)cw * N + j] = L[j];
+        if (p.post)
+            for (int j = tid; j < N; j += nthr) p.post[(size_t)cw * N + j] = L[j];
         __syncthreads();
     }
 }
@@ -164,12 +177,22 @@ __global__ void __launch_bounds__(512, 1) learned_bwd_kernel(LearnedParams p) {
         float *C = P + (size_t)p.T * N;
         float *V = C + (size_t)p.T * EZ;
         float *G = V + EZ;
-        for (int j = tid; j < N; j += nthr) gL[j] = p.grad_post[(size_t)cw * N + j];
+        const float *g_last =
+            p.grad_post_iter ? p.grad_post_iter + ((size_t)(p.T - 1) * p.batch + cw) * N
+                             : p.grad_post + (size_t)cw * N;
+        for (int j = tid; j < N; j += nthr) gL[j] = g_last[j];
         for (int k = tid; k < EZ; k += nthr) G[k] = 0.0f;
         __syncthreads();
         for (int t = p.T - 1; t >= 0; --t) {
-            // replay iteration t from its checkpoint, keeping every v
-            for (int j = tid; j < N; j += nthr) L[j] = P[(size_t)t * N + j];
+            // adjoint of this iteration's own output term; replay iteration t from its
+            // checkpoint, keeping every v
+            const float *g_t = (p.grad_post_iter && t < p.T - 1)
+                                   ? p.grad_post_iter + ((size_t)t * p.batch + cw) * N
+                                   : nullptr;
+            for (int j = tid; j < N; j += nthr) {
+                L[j] = P[(size_t)t * N + j];
+                if (g_t) gL[j] += g_t[j];
+            }
             __syncthreads();
             const float *c_old = t ? C + (size_t)(t - 1) * EZ : nullptr;
             for (int r = 0; r < n_rows; ++r) {
@@ -261,8 +284,11 @@ size_t learned_ws_floats_per_cw(int N, int EZ, int T) {
 
 ldpc_status launch_learned(const DecodeParams &dp, int T, const float *params, const float *llr,
                            float *post, const float *grad_post, float *grad_params,
-                           float *grad_llr, float *ws, bool backward, cudaStream_t stream) {
+                           float *grad_llr, float *ws, bool backward, cudaStream_t stream,
+                           float *post_iter, const float *grad_post_iter) {
     LearnedParams p;
+    p.post_iter = post_iter;
+    p.grad_post_iter = grad_post_iter;
     p.edges = dp.edges;
     p.row_ptr = dp.row_ptr;
     p.n_rows = dp.n_rows;

@@ -530,6 +530,32 @@ ldpc_status ldpc_learned_backward(ldpc_graph_t h, const float *grad_post, int ba
                                 ws, true, reinterpret_cast<cudaStream_t>(stream));
 }
 
+ldpc_status ldpc_learned_forward_iter(ldpc_graph_t h, const float *llr, int batch, int T,
+                                      int n_rows, int n_tx, const float *params,
+                                      ldpc_stream_t stream, float *post_iter, float *ws) {
+    ldpc::DecodeParams p;
+    ldpc_status st = learned_common(h, batch, T, n_rows, n_tx, &p);
+    if (st != LDPC_OK) return st;
+    if (batch == 0) return LDPC_OK;
+    if (!llr || !params || !post_iter || !ws) return LDPC_ERR_INVALID_ARG;
+    return ldpc::launch_learned(p, T, params, llr, nullptr, nullptr, nullptr, nullptr, ws, false,
+                                reinterpret_cast<cudaStream_t>(stream), post_iter, nullptr);
+}
+
+ldpc_status ldpc_learned_backward_iter(ldpc_graph_t h, const float *grad_post_iter, int batch,
+                                       int T, int n_rows, int n_tx, const float *params,
+                                       ldpc_stream_t stream, float *ws, float *grad_params,
+                                       float *grad_llr) {
+    ldpc::DecodeParams p;
+    ldpc_status st = learned_common(h, batch, T, n_rows, n_tx, &p);
+    if (st != LDPC_OK) return st;
+    if (batch == 0) return LDPC_OK;
+    if (!grad_post_iter || !params || !ws || !grad_params) return LDPC_ERR_INVALID_ARG;
+    return ldpc::launch_learned(p, T, params, nullptr, nullptr, nullptr, grad_params, grad_llr,
+                                ws, true, reinterpret_cast<cudaStream_t>(stream), nullptr,
+                                grad_post_iter);
+}
+
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t h, ldpc_stream_t stream) {
     if (!h) return LDPC_ERR_INVALID_ARG;
     Graph *g = reinterpret_cast<Graph *>(h);

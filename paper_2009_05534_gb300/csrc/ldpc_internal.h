@@ -79,11 +79,17 @@ ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream);
 bool rowpair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stream);
 
+// binary16 decoder with messages in Tensor Memory, all three corrections
+// (decode_tmem16.cu).
+bool tmem16_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
+ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream);
+
 // Learned min-sum forward / backward (decode_learned.cu); ws holds the checkpoints.
 size_t learned_ws_floats_per_cw(int N, int EZ, int T);
 ldpc_status launch_learned(const DecodeParams &dp, int T, const float *params, const float *llr,
                            float *post, const float *grad_post, float *grad_params,
-                           float *grad_llr, float *ws, bool backward, cudaStream_t stream);
+                           float *grad_llr, float *ws, bool backward, cudaStream_t stream,
+                           float *post_iter = nullptr, const float *grad_post_iter = nullptr);
 
 // Work-list decode (decode_rowpair.cu): items are taken dynamically through *d_counter,
 // which must be zero at launch.

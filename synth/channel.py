@@ -22,6 +22,8 @@ channel used for the synthetic workloads:
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -31,7 +33,29 @@ NOISE_STREAM = 2
 
 
 def std_normals(seed: int, batch: int, n: int, first_cw: int = 0) -> np.ndarray:
-    """Seeded standard normals, float64 [batch][n]."""
+    """Seeded standard normals, float64 [batch][n].
+
+    Every value depends only on its own counter, so large requests are split over
+    codeword ranges and generated on a thread pool (numpy releases the GIL inside its
+    element-wise loops); the result is the same as one call over the whole range.
+    """
+    nblk = (n + 3) // 4
+    workers = min(os.cpu_count() or 1, 16)
+    if workers > 1 and batch >= 2 * workers and batch * nblk >= (1 << 20):
+        out = np.empty((batch, n), dtype=np.float64)
+        cuts = np.linspace(0, batch, workers + 1).astype(int)
+
+        def part(i):
+            lo, hi = int(cuts[i]), int(cuts[i + 1])
+            out[lo:hi] = _std_normals(seed, hi - lo, n, first_cw + lo)
+
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(part, range(workers)))
+        return out
+    return _std_normals(seed, batch, n, first_cw)
+
+
+def _std_normals(seed: int, batch: int, n: int, first_cw: int) -> np.ndarray:
     k0, k1 = seed_key(seed)
     nblk = (n + 3) // 4
     j = np.arange(nblk, dtype=np.uint64)[None, :]
@@ -49,6 +73,19 @@ def std_normals(seed: int, batch: int, n: int, first_cw: int = 0) -> np.ndarray:
         out[:, :, k] = r * np.cos(th)
         out[:, :, k + 1] = r * np.sin(th)
     return out.reshape(batch, nblk * 4)[:, :n]
+
+
+EBN0_STREAM = 4
+
+
+def uniform_ebn0(seed: int, batch: int, lo: float, hi: float, first_cw: int = 0) -> np.ndarray:
+    """Per-codeword Eb/N0 in dB, uniform in [lo, hi): codeword b uses word 0 of the Philox
+    counter (b, 4, 0, 0)."""
+    k0, k1 = seed_key(seed)
+    cw = np.arange(batch, dtype=np.uint64) + np.uint64(first_cw)
+    w = philox4x32(cw, EBN0_STREAM, 0, 0, k0, k1)[0]
+    u = (w.astype(np.float64) + 0.5) / 4294967296.0
+    return lo + (hi - lo) * u
 
 
 def noise_n0(ebn0_db: float, rate: float, bits_per_symbol: int) -> float:
@@ -108,30 +145,42 @@ def pam_maxlog_llr(y: np.ndarray, mh: int, n0: float) -> np.ndarray:
     return out
 
 
-def modulate_llr(bits: np.ndarray, ebn0_db: float, rate: float, modulation: str,
+_BITS_PER_SYMBOL = {"BPSK": 1, "QPSK": 2, "16QAM": 4, "64QAM": 6}
+
+
+def modulate_llr(bits: np.ndarray, ebn0_db, rate: float, modulation: str,
                  seed: int, first_cw: int = 0) -> np.ndarray:
-    """Channel LLRs (float32 [B][n]) for transmitted bits [B][n] over AWGN."""
+    """Channel LLRs (float32 [B][n]) for transmitted bits [B][n] over AWGN.
+
+    ebn0_db is one value for the whole batch or an array [B] with one value per codeword;
+    a codeword's LLRs do not depend on which of the two forms carried its Eb/N0.
+    """
     B, n = bits.shape
-    if modulation in ("BPSK", "QPSK"):
-        m = 1 if modulation == "BPSK" else 2
-        A = 1.0 if m == 1 else 1.0 / math.sqrt(2.0)
-        n0 = noise_n0(ebn0_db, rate, m)
+    m = _BITS_PER_SYMBOL.get(modulation)
+    if m is None:
+        raise ValueError(f"unknown modulation {modulation}")
+    if np.ndim(ebn0_db) == 0:
+        n0 = noise_n0(float(ebn0_db), rate, m)
         sigma = math.sqrt(n0 / 2.0)
+    else:
+        e = np.asarray(ebn0_db, dtype=np.float64).reshape(-1)
+        if e.shape != (B,):
+            raise ValueError("per-codeword Eb/N0 needs one value per codeword")
+        n0s = [noise_n0(float(x), rate, m) for x in e]
+        n0 = np.array(n0s)[:, None]
+        sigma = np.array([math.sqrt(v / 2.0) for v in n0s])[:, None]
+    if m <= 2:
+        A = 1.0 if m == 1 else 1.0 / math.sqrt(2.0)
         y = A * (1.0 - 2.0 * bits.astype(np.float64)) + sigma * std_normals(seed, B, n, first_cw)
         return (4.0 * A * y / n0).astype(np.float32)
-    if modulation in ("16QAM", "64QAM"):
-        m = 4 if modulation == "16QAM" else 6
-        mh = m // 2
-        n0 = noise_n0(ebn0_db, rate, m)
-        sigma = math.sqrt(n0 / 2.0)
-        nsym_dims = (n + mh - 1) // mh                  # real dimensions used
-        pad = nsym_dims * mh - n
-        bp = np.concatenate([bits, np.zeros((B, pad), dtype=bits.dtype)], axis=1)
-        x = pam_map(bp.reshape(B, nsym_dims, mh), mh)
-        y = x + sigma * std_normals(seed, B, nsym_dims, first_cw)
-        llr = pam_maxlog_llr(y, mh, n0)
-        return llr.reshape(B, nsym_dims * mh)[:, :n].astype(np.float32)
-    raise ValueError(f"unknown modulation {modulation}")
+    mh = m // 2
+    nsym_dims = (n + mh - 1) // mh                      # real dimensions used
+    pad = nsym_dims * mh - n
+    bp = np.concatenate([bits, np.zeros((B, pad), dtype=bits.dtype)], axis=1)
+    x = pam_map(bp.reshape(B, nsym_dims, mh), mh)
+    y = x + sigma * std_normals(seed, B, nsym_dims, first_cw)
+    llr = pam_maxlog_llr(y, mh, n0)
+    return llr.reshape(B, nsym_dims * mh)[:, :n].astype(np.float32)
 
 
 def quantize_int8(llr: np.ndarray, scale: float = 4.0) -> np.ndarray:

@@ -48,13 +48,15 @@ class Workload:
         return to_fp16(self.llr)
 
 
-def make_workload(kind: str, Z: int, batch: int, ebn0_db: float, rate=None,
+def make_workload(kind: str, Z: int, batch: int, ebn0_db, rate=None,
                   modulation: str = "QPSK", seed: int = 0, graph_seed: int | None = None,
                   punct_cols: int = 2, first_cw: int = 0, noiseless_llr: float | None = None,
                   base: np.ndarray | None = None) -> Workload:
     """Build a workload.  rate=None uses every base row (the lowest rate of the graph).
 
     noiseless_llr: if given, LLRs are +/- that value with no noise (the P2 pin).
+    ebn0_db: one value, or an array with one value per codeword (the mean is kept in
+    ``ebn0_db`` and the array in ``meta["ebn0_db"]``).
     """
     sh = SHAPES[kind]
     if base is None:
@@ -75,5 +77,8 @@ def make_workload(kind: str, Z: int, batch: int, ebn0_db: float, rate=None,
         llr = (noiseless_llr * (1.0 - 2.0 * tx.astype(np.float32))).astype(np.float32)
     else:
         llr = modulate_llr(tx, ebn0_db, R, modulation, seed, first_cw)
+    meta = {"rate": R, "seed": seed}
+    if np.ndim(ebn0_db) != 0:
+        meta["ebn0_db"] = np.asarray(ebn0_db, dtype=np.float64)
     return Workload(kind, Z, base, sh.K_b, n_rows, n_tx, punct_cols, u, cw, llr,
-                    float(ebn0_db), modulation, {"rate": R, "seed": seed})
+                    float(np.mean(ebn0_db)), modulation, meta)

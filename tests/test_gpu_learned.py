@@ -49,9 +49,40 @@ def test_forward_and_gradient_match_oracle(ldpc, kind, Z, T):
     gp, gl = learned.backward(g, gpost, pt, ws, n_tx=wl.n_tx, want_grad_llr=True)
     torch.cuda.synchronize()
     gp = gp.sum(0).cpu().numpy().astype(np.float64)
-    scale = np.abs(gp_o).max()
-    assert np.allclose(gp, gp_o, rtol=1e-3, atol=1e-4 * scale)
+    for t in range(T):                  # each iteration at its own scale
+        scale = np.abs(gp_o[t]).max()
+        assert np.allclose(gp[t], gp_o[t], rtol=1e-3, atol=1e-4 * scale), t
     assert np.allclose(gl.cpu().numpy(), gl_o, rtol=1e-3, atol=1e-4 * np.abs(gl_o).max())
+    g.close()
+
+
+@pytest.mark.parametrize("kind,Z,T", [("BG2", 16, 4), ("BG1", 32, 3)])
+def test_every_iteration_loss_matches_oracle(ldpc, kind, Z, T):
+    """Per-iteration posteriors equal the oracle's decodes stopped after t + 1 iterations,
+    and the gradient of the iteration-weighted BCE (through the autograd wrapper) matches
+    the oracle's."""
+    from paper_2009_05534_gb300 import learned
+    wl = make_workload(kind, Z, 5, 1.5, modulation="BPSK", seed=Z + 1)
+    prm = _params(T, wl.n_rows, Z + 1)
+    w = np.linspace(0.5, 1.5, T)
+    g = ldpc.Graph(wl.base, wl.K_b, Z)
+    llr = torch.from_numpy(wl.llr).cuda()
+    pt = torch.from_numpy(prm).cuda().requires_grad_(True)
+    post = learned.learned_decode(pt, llr, g, 0, wl.n_tx, every_iteration=True)
+    for t in range(T):
+        ref = oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, wl.llr, algo=oracle.LEARNED,
+                                    learned=prm[:t + 1], max_iter=t + 1, early_stop=False,
+                                    want_post=True)
+        assert np.array_equal(post[t].detach().cpu().numpy(), ref.post)
+    cw = torch.from_numpy(wl.codewords).cuda()
+    loss = learned.bce_loss(post, cw, torch.tensor(w, dtype=torch.float32, device="cuda"))
+    loss.backward()
+    loss_o, gp_o, _, _ = oracle.learned_grad(wl.base, wl.K_b, Z, wl.n_rows, wl.llr, prm,
+                                             wl.codewords, iter_weights=w)
+    assert abs(float(loss.detach()) - loss_o) < 1e-4 * abs(loss_o)
+    gp = pt.grad.cpu().numpy().astype(np.float64)
+    for t in range(T):
+        assert np.allclose(gp[t], gp_o[t], rtol=1e-3, atol=1e-4 * np.abs(gp_o[t]).max()), t
     g.close()
 
 

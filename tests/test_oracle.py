@@ -279,6 +279,36 @@ def test_fp16_close_to_fp32():
     assert np.median(rel) < 2 ** -7
 
 
+@pytest.mark.parametrize("mode", ["normalised", "offset", "learned"])
+def test_fp16_parameters_enter_as_binary16(mode):
+    """In the binary16 decoder a correction parameter acts only through its binary16 value:
+    alpha = 0.7 and alpha = fl16(0.7) decode identically, and differently from fl16(0.7)
+    moved by one binary16 step."""
+    wl = make_workload("BG2", 16, 8, 1.5, modulation="BPSK", seed=4)
+    h = wl.llr_fp16()
+    T = 3
+
+    def run(x):
+        if mode == "normalised":
+            kw = dict(algo=oracle.NORMALISED, alpha=x)
+        elif mode == "offset":
+            kw = dict(algo=oracle.OFFSET, offset=x)
+        else:
+            tab = np.zeros((T, wl.n_rows, 2), np.float32)
+            tab[..., 0] = x
+            tab[..., 1] = x / 4
+            kw = dict(algo=oracle.LEARNED, learned=tab)
+        return oracle.decode_layered(wl.base, wl.K_b, 16, wl.n_rows, h, max_iter=T,
+                                     early_stop=False, want_post=True, **kw).post
+
+    x = 0.7 if mode != "offset" else 0.3
+    x16 = float(np.float16(x))
+    assert x16 != x
+    assert np.array_equal(run(x), run(x16))
+    step = float(np.nextafter(np.float16(x16), np.float16(1.0)))
+    assert not np.array_equal(run(x16), run(step))
+
+
 def test_early_stop_semantics():
     wl = make_workload("BG2", 16, 40, 4.0, modulation="BPSK", seed=1)
     ra = oracle.decode_layered(wl.base, wl.K_b, 16, wl.n_rows, wl.llr, max_iter=8,

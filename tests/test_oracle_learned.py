@@ -112,3 +112,56 @@ def test_structural_zeros():
     c = wl.codewords[:, 2 * Z:2 * Z + wl.n_tx].astype(np.float64)
     want = (c - 1.0 / (1.0 + np.exp(L))) / (wl.llr.shape[0] * N)
     assert np.allclose(gl, want, rtol=1e-6, atol=1e-12)
+
+
+# ------------------------------------------------------- loss over every iteration's output
+
+def test_iteration_weighted_loss_value_and_split():
+    """loss(w) = sum_t w_t * BCE(posteriors after iteration t): the value equals the BCE of
+    layered decodes stopped after t + 1 iterations, and the gradient of the term of
+    iteration t equals the final-loss gradient of the table cut after iteration t (later
+    iterations have no influence on it)."""
+    T = 3
+    wl, params = _setup(kind="BG2", Z=4, B=3, T=T, seed=12)
+    w = np.array([0.5, 0.25, 1.0])
+    loss, gp, _, _ = oracle.learned_grad(wl.base, wl.K_b, wl.Z, wl.n_rows, wl.llr, params,
+                                         wl.codewords, iter_weights=w)
+    want = 0.0
+    for t in range(T):
+        r = oracle.decode_layered(wl.base, wl.K_b, wl.Z, wl.n_rows, wl.llr,
+                                  algo=oracle.LEARNED, learned=params[:t + 1],
+                                  max_iter=t + 1, early_stop=False, want_post=True)
+        want += w[t] * _loss_from_post(r.post, wl.codewords, r.post.shape[1])
+    assert abs(loss - want) < 1e-9
+    total = np.zeros_like(gp)
+    for t in range(T):
+        e = np.zeros(T)
+        e[t] = 1.0
+        _, g_t, _, _ = oracle.learned_grad(wl.base, wl.K_b, wl.Z, wl.n_rows, wl.llr, params,
+                                           wl.codewords, iter_weights=e)
+        _, g_cut, _, _ = oracle.learned_grad(wl.base, wl.K_b, wl.Z, wl.n_rows, wl.llr,
+                                             params[:t + 1], wl.codewords)
+        assert np.all(g_t[t + 1:] == 0.0)
+        assert np.allclose(g_t[:t + 1], g_cut, rtol=1e-12, atol=1e-15)
+        total += w[t] * g_t
+    assert np.allclose(gp, total, rtol=1e-9, atol=1e-15)
+
+
+def test_iteration_weighted_gradient_finite_differences():
+    T = 3
+    wl = make_workload("TINY", 3, 4, 2.0, modulation="BPSK", seed=13, punct_cols=0)
+    rng = np.random.default_rng(13)
+    params = np.zeros((T, wl.n_rows, 2), np.float32)
+    params[..., 0] = rng.uniform(0.6, 1.0, size=(T, wl.n_rows))
+    params[..., 1] = rng.uniform(0.0, 0.3, size=(T, wl.n_rows))
+    w = np.array([1.0, 0.5, 2.0])
+
+    def f(p):
+        return oracle.learned_grad(wl.base, wl.K_b, wl.Z, wl.n_rows, wl.llr, p, wl.codewords,
+                                   punct=0, iter_weights=w)[0]
+
+    _, gp, _, _ = oracle.learned_grad(wl.base, wl.K_b, wl.Z, wl.n_rows, wl.llr, params,
+                                      wl.codewords, punct=0, iter_weights=w)
+    idx = [(t, r, k) for t in range(T) for r in range(wl.n_rows) for k in range(2)]
+    ok, bad = _fd_agreement(f, params, gp, idx)
+    assert ok >= 8 and bad <= 0.1 * (ok + bad), (ok, bad)

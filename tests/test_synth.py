@@ -200,3 +200,22 @@ def test_quantize_int8():
     assert q.tolist() == [0, 2, 0, -2, 127, 127, -127, 0, 10]
     big = quantize_int8(np.linspace(-1000, 1000, 10001, dtype=np.float32))
     assert big.min() == -127 and big.max() == 127
+
+
+@pytest.mark.parametrize("mod", ["BPSK", "QPSK", "16QAM", "64QAM"])
+def test_per_codeword_ebn0_matches_scalar(mod):
+    """A batch with one Eb/N0 per codeword equals each codeword generated alone."""
+    e = np.array([0.5, 1.0, 2.5, 1.0, 0.7])
+    w = make_workload("BG2", 16, 5, e, modulation=mod, seed=3, graph_seed=0)
+    assert np.array_equal(w.meta["ebn0_db"], e)
+    for b in range(5):
+        w1 = make_workload("BG2", 16, 1, float(e[b]), modulation=mod, seed=3, graph_seed=0,
+                           first_cw=b)
+        assert np.array_equal(w1.llr[0], w.llr[b])
+
+
+def test_threaded_normals_match_single_range():
+    from synth.channel import _std_normals, std_normals
+    a = std_normals(11, 700, 6001, first_cw=5)          # large enough to take the pool
+    assert np.array_equal(a, _std_normals(11, 700, 6001, 5))
+    assert np.array_equal(a[123], _std_normals(11, 1, 6001, 5 + 123)[0])
