@@ -178,11 +178,13 @@ SERVE_RATES = ("1/3", "1/2", "2/3", "5/6", "8/9")
 SERVE_MODS = (("QPSK", 3.0), ("16QAM", 7.0), ("64QAM", 11.0))
 
 
-def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_iter: int = 10):
+def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_iter: int = 10,
+                    learned_share: float = 0.125):
     """Mixed-traffic slot serving: Poisson(mean_tbs) transport blocks per 500 us slot
     (clipped to 64..512), each a uniformly drawn (BG1|BG2, Z, rate, modulation) codeword
-    from a device-resident pool of synthetic int8 LLRs; returns p50/p99 latency and
-    throughput."""
+    from a device-resident pool of synthetic int8 LLRs, plus (share `learned_share`, when
+    the trained table is present) learned-decoder blocks (BG2-shaped Z=128, every row,
+    binary16 QPSK LLRs); returns p50/p99 latency and throughput."""
     from fractions import Fraction
 
     import numpy as np
@@ -214,7 +216,25 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
     pick = rng.integers(0, len(pool), size=total)
     table, kreq = pool[pick], ks[pick]
     kmax = max(g.K for g in graphs.values())
-    be = GpuBackend(table, kreq, n_buffers=4096, kmax=kmax, n_streams=4, early_stop=True)
+    learned, n_learned = None, 0
+    path = os.path.join(ROOT, "paper_2009_05534_gb300", "tables", LEARNED_TABLE)
+    if learned_share > 0 and os.path.exists(path):
+        from paper_2009_05534_gb300.serve import LearnedClass
+        from paper_2009_05534_gb300.train_learned import load_table
+        tab, meta = load_table(path)
+        wl = make_workload("BG2", 128, 256, 3.0, modulation="QPSK", seed=seed * 1000 + 999,
+                           graph_seed=0)
+        g_l = graphs[("BG2", 128)]
+        lpool = torch.from_numpy(wl.llr_fp16()).cuda()
+        is_l = rng.random(total) < learned_share
+        lpick = np.where(is_l, rng.integers(0, len(lpool), size=total), -1).astype(np.int32)
+        kreq = np.where(is_l, wl.K, kreq)
+        n_learned = int(is_l.sum())
+        learned = LearnedClass(g_l, lpool, torch.from_numpy(tab).cuda(), lpick,
+                               int(meta["T"]), 0)
+        ldpc.decode(g_l, lpool[:8], learned.max_iter, algo=ldpc.LEARNED, learned=learned.table)
+    be = GpuBackend(table, kreq, n_buffers=4096, kmax=kmax, n_streams=4, early_stop=True,
+                    learned=learned)
     sch = SlotScheduler(be, slot_us=500.0, max_requests=total + 1)
     # warm-up: a few slots outside the measurement
     warm = SlotScheduler(GpuBackend(np.tile(pool, 4), np.tile(ks, 4), n_buffers=1024,
@@ -229,8 +249,38 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
     return {"slots": n_slots, "slot_us": 500.0, "tbs": total, "mean_tbs_per_slot":
             float(counts.mean()), "p50_us": st.get("p50_us"), "p99_us": st.get("p99_us"),
             "max_us": st.get("max_us"), "gbps": float(kreq.sum()) / wall / 1e9,
-            "max_iter": max_iter, "early_stop": True,
-            "traffic": "BG1|BG2 x Z{32..384} x R{1/3..8/9} x QPSK/16QAM/64QAM int8"}
+            "max_iter": max_iter, "early_stop": True, "learned_tbs": n_learned,
+            "traffic": "BG1|BG2 x Z{32..384} x R{1/3..8/9} x QPSK/16QAM/64QAM int8"
+                       + (f"; {learned_share:.3f} of blocks learned (BG2 Z=128 R=1/5 "
+                          "binary16, 10 iterations)" if learned is not None else "")}
+
+
+# ------------------------------------------------------------------- single-codeword latency
+
+def latency_measure(wl, graph, reps: int = 50):
+    """Latency of one codeword alone (batch 1, the headline workload, 10 iterations, early
+    stop off): CUDA events around each launch on an otherwise idle stream; median and max."""
+    import torch
+
+    import paper_2009_05534_gb300 as ldpc
+    stream = torch.cuda.Stream()
+    q = torch.from_numpy(wl.llr_int8()[:1]).cuda()
+    out = {}
+    for name, dt in (("int8", q), ("fp16", torch.from_numpy(wl.llr_fp16()[:1]).cuda())):
+        kw = dict(algo=ldpc.OFFSET) if name == "int8" else dict(algo=ldpc.NORMALISED,
+                                                                alpha=0.75)
+        ts = []
+        for k in range(reps + 3):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            ldpc.decode(graph, dt, T_ITER, early_stop=False, stream=stream, **kw)
+            e.record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(s.elapsed_time(e) * 1e3)
+        out[name] = {"median_us": statistics.median(ts), "max_us": max(ts),
+                     "per_iteration_us": statistics.median(ts) / T_ITER}
+    return {"workload": "one BG1-shaped Z=384 R=1/3 codeword, 10 iterations", **out}
 
 
 # ------------------------------------------------------------------- high load (R = 8/9)
@@ -304,8 +354,9 @@ def high_load_measure(batch: int = 8192, caps=(5, 10, 20), reps: int = 5, seed: 
 LEARNED_TABLE = "learned_bg2_z128_t10.json"
 
 
-def learned_measure(n_cw: int = 8192, grid=(3.0, 3.25, 3.5, 3.75, 4.0, 4.25), batch: int = 8192,
-                    reps: int = 5):
+def learned_measure(n_cw: int = 8192,
+                    grid=(1.5, 1.75, 2.0, 2.25, 2.5, 2.75, 3.0, 3.5, 3.75, 4.0, 4.25),
+                    batch: int = 8192, reps: int = 5):
     """The trained (beta, gamma) table against plain normalised min-sum (alpha 0.75) on the
     same fresh codewords: BLER per Eb/N0 at T = 10 (binary16 LLRs and messages), the Eb/N0
     of BLER 1e-2 for each, and decode throughput of both at T = 10 and, with early stop,
@@ -359,7 +410,7 @@ def learned_measure(n_cw: int = 8192, grid=(3.0, 3.25, 3.5, 3.75, 4.0, 4.25), ba
             "gain_db": (at["plain"] - at["learned"]) if None not in at.values() else None,
             "throughput_ebn0_db": eb_op, "throughput": thr,
             "training": {k: meta["training"].get(k) for k in
-                         ("codewords", "epochs", "steps", "lr", "ebn0_db", "loss")}}
+                         ("codewords", "epochs", "steps", "lr", "ebn0_db", "loss", "gradient")}}
 
 
 # ----------------------------------------------------------------------------- reference
@@ -518,6 +569,7 @@ def run_ours(args):
     traffic = profiled_traffic("layered_int8_bg1_z384")
 
     serving = serving_measure(args.serve_slots) if args.serve_slots > 0 else None
+    latency = latency_measure(wl, graph)
     high_load = high_load_measure() if args.high_load else None
     learned = learned_measure() if args.learned else None
 
@@ -552,6 +604,7 @@ def run_ours(args):
             "e2e": {"value": e2e, "unit": "Gbit/s", "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": B * (nbytes + 4)},
             "serving": serving,
+            "latency": latency,
             "high_load": high_load,
             "learned": learned,
             "gpu_launches": launches,

@@ -49,7 +49,12 @@ typedef enum {
 } ldpc_status;
 
 typedef enum { LDPC_LLR_INT8 = 0, LDPC_LLR_FP16 = 1, LDPC_LLR_FP32 = 2 } ldpc_llr_type;
-typedef enum { LDPC_NORMALISED = 0, LDPC_OFFSET = 1, LDPC_LEARNED = 2 } ldpc_algo;
+typedef enum {
+    LDPC_NORMALISED = 0,
+    LDPC_OFFSET = 1,
+    LDPC_LEARNED = 2,
+    LDPC_SUM_PRODUCT = 3      /* flooding decoder only (ldpc_decode_flooding) */
+} ldpc_algo;
 
 /* Decoder options.  Fill with ldpc_decode_opts_default() and change what you need.
  *   llr_type     element type of the channel LLRs, posteriors and messages.
@@ -116,6 +121,18 @@ int ldpc_graph_vars(ldpc_graph_t g, int n_rows);
 ldpc_status ldpc_decode(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
                         ldpc_stream_t stream, const ldpc_decode_opts *opts,
                         uint8_t *hard_bits_dev, int32_t *iters_dev);
+
+/* Batch decode through row maps (serving support; the paper has no counterpart): codeword
+ * b of the batch reads channel LLR row in_rows_dev[b] of llr_dev and writes hard-bit row
+ * out_rows_dev[b] of hard_bits_dev and entry out_rows_dev[b] of iters_dev, so requests
+ * scattered over a device pool decode in one launch without a gather.
+ *   in_rows_dev, out_rows_dev  device int32 [batch]; rows must lie inside the caller's
+ *                              buffers, and out rows must be distinct.
+ * Everything else as for ldpc_decode. */
+ldpc_status ldpc_decode_rows(ldpc_graph_t g, const void *llr_dev, const int32_t *in_rows_dev,
+                             const int32_t *out_rows_dev, int batch, int max_iter,
+                             ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                             uint8_t *hard_bits_dev, int32_t *iters_dev);
 
 /* As ldpc_decode, and also writes the final posteriors and check-to-variable messages
  * (for parity tests):
@@ -223,8 +240,11 @@ ldpc_status ldpc_learned_backward(ldpc_graph_t g, const float *grad_post_dev, in
  * Other arguments, the workspace contract and the outputs are those of
  * ldpc_learned_forward / ldpc_learned_backward.  The reverse sweep adds the adjoint of
  * slice t when it reaches the end of iteration t + 1, so grad_params is the gradient of
- * the loss summed over all slices.  Not in the paper (training support, like the functions
- * above). */
+ * the loss summed over all slices.  detach != 0 resets the adjoints at every iteration
+ * boundary instead: the parameters of iteration t + 1 then get the partial derivative of
+ * slice t's own loss term (exact for that term; later terms' contributions are dropped) and
+ * grad_llr only the contribution through iteration 1.  Not in the paper (training support,
+ * like the functions above). */
 ldpc_status ldpc_learned_forward_iter(ldpc_graph_t g, const float *llr_dev, int batch, int T,
                                       int n_rows, int n_tx, const float *params_dev,
                                       ldpc_stream_t stream, float *post_iter_dev,
@@ -233,7 +253,28 @@ ldpc_status ldpc_learned_backward_iter(ldpc_graph_t g, const float *grad_post_it
                                        int batch, int T, int n_rows, int n_tx,
                                        const float *params_dev, ldpc_stream_t stream,
                                        float *workspace_dev, float *grad_params_dev,
-                                       float *grad_llr_dev);
+                                       float *grad_llr_dev, int detach);
+
+/* ---- Flooding schedule (the comparison baseline of Sec. V) -------------------------
+ * Every check row of every used base row is updated from the posteriors of the previous
+ * iteration; then every posterior is recomputed as its channel LLR plus its incoming
+ * messages summed in base-row order (the posterior equation of Sec. III); then the
+ * syndrome test of ldpc_decode.  fp32 LLRs only (opts->llr_type must be LDPC_LLR_FP32);
+ * opts->algo selects min-sum with LDPC_NORMALISED / LDPC_OFFSET, or LDPC_SUM_PRODUCT: the
+ * exact tanh rule (Sec. III), evaluated in binary64 with the product over the other edges
+ * clamped to +-(1 - 1e-15) before atanh.  Other options as for ldpc_decode.
+ *   llr_dev        device float [batch][n_tx]
+ *   bits_dev, iters_dev  as for ldpc_decode
+ *   post_dev       device float [batch][(K_b + n_rows) * Z] final posteriors, or NULL
+ *   workspace_dev  caller-owned device memory of ldpc_flooding_workspace_floats(g, batch,
+ *                  n_rows) floats (the check-to-variable messages); overwritten.
+ * Errors: LDPC_ERR_INVALID_ARG for bad arguments, LDPC_ERR_UNSUPPORTED for shapes beyond
+ * 1024 edges, row degree 24 or the shared-memory size of one codeword's posteriors. */
+size_t ldpc_flooding_workspace_floats(ldpc_graph_t g, int batch, int n_rows);
+ldpc_status ldpc_decode_flooding(ldpc_graph_t g, const float *llr_dev, int batch, int max_iter,
+                                 ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                                 uint8_t *hard_bits_dev, int32_t *iters_dev, float *post_dev,
+                                 float *workspace_dev);
 
 /* Wait for the graph's outstanding work on `stream` and return (then clear) the device
  * status word: LDPC_OK, or the first error a kernel reported (e.g. LDPC_ERR_TIMEOUT). */

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libldpc.so")
 
 LLR_INT8, LLR_FP16, LLR_FP32 = 0, 1, 2
-NORMALISED, OFFSET, LEARNED = 0, 1, 2
+NORMALISED, OFFSET, LEARNED, SUM_PRODUCT = 0, 1, 2, 3
 
 _STATUS = {0: "LDPC_OK", 1: "LDPC_ERR_INVALID_ARG", 2: "LDPC_ERR_UNSUPPORTED",
            3: "LDPC_ERR_OUT_OF_MEMORY", 4: "LDPC_ERR_CUDA", 5: "LDPC_ERR_TIMEOUT"}
@@ -51,7 +51,10 @@ _lock = threading.Lock()
 ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_destroy",
                "ldpc_graph_edges", "ldpc_graph_vars", "ldpc_decode", "ldpc_decode_debug",
                "ldpc_graph_sync_status", "ldpc_status_string", "ldpc_launch_count",
-               "ldpc_decode_host", "ldpc_decode_list", "ldpc_decode_list_noalloc")
+               "ldpc_decode_host", "ldpc_decode_list", "ldpc_decode_list_noalloc",
+               "ldpc_learned_workspace_floats", "ldpc_learned_forward", "ldpc_learned_backward",
+               "ldpc_learned_forward_iter", "ldpc_learned_backward_iter",
+               "ldpc_flooding_workspace_floats", "ldpc_decode_flooding", "ldpc_decode_rows")
 
 
 def lib():
@@ -93,6 +96,14 @@ def lib():
             L.ldpc_status_string.restype = ctypes.c_char_p
             L.ldpc_launch_count.argtypes = []
             L.ldpc_launch_count.restype = ctypes.c_uint64
+            L.ldpc_decode_rows.argtypes = [P, P, P, P, i, i, P, ctypes.POINTER(DecodeOpts),
+                                           P, P]
+            L.ldpc_decode_rows.restype = i
+            L.ldpc_flooding_workspace_floats.argtypes = [P, i, i]
+            L.ldpc_flooding_workspace_floats.restype = ctypes.c_size_t
+            L.ldpc_decode_flooding.argtypes = [P, P, i, i, P, ctypes.POINTER(DecodeOpts), P, P,
+                                               P, P]
+            L.ldpc_decode_flooding.restype = i
             _lib = L
     return _lib
 
@@ -199,6 +210,7 @@ def decode(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stream=No
     llr = llr.contiguous()
     B = llr.shape[0]
     lt = _llr_type(llr)
+    kw.setdefault("n_tx", llr.shape[1])          # one LLR row per codeword
     o = make_opts(lt, **kw)
     nb = (graph.K + 7) // 8
     dev = llr.device
@@ -224,6 +236,62 @@ def decode(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stream=No
     return bits, iters, post, c2v
 
 
+def decode_rows(graph: Graph, llr, in_rows, out_rows, max_iter: int, *, bits, iters,
+                stream=None, **kw):
+    """Decode codewords llr[in_rows[b]] (a CUDA pool [rows][n_tx]) into bits[out_rows[b]] and
+    iters[out_rows[b]]; in_rows / out_rows are int32 CUDA tensors of the batch length."""
+    import torch
+    if not (llr.is_cuda and in_rows.is_cuda and out_rows.is_cuda):
+        raise ValueError("llr and the row maps must be CUDA tensors")
+    if in_rows.dtype != torch.int32 or out_rows.dtype != torch.int32:
+        raise TypeError("row maps must be int32")
+    n = in_rows.numel()
+    if out_rows.numel() != n:
+        raise ValueError("row maps differ in length")
+    if n and (int(in_rows.max()) >= llr.shape[0] or int(out_rows.max()) >= bits.shape[0]
+              or int(in_rows.min()) < 0 or int(out_rows.min()) < 0):
+        raise ValueError("row map outside the buffers")
+    llr = llr.contiguous()
+    kw.setdefault("n_tx", llr.shape[1])
+    o = make_opts(_llr_type(llr), **kw)
+    _check(lib().ldpc_decode_rows(graph.handle, ctypes.c_void_p(llr.data_ptr()),
+                                  ctypes.c_void_p(in_rows.data_ptr()),
+                                  ctypes.c_void_p(out_rows.data_ptr()), n, int(max_iter),
+                                  _stream_ptr(stream), ctypes.byref(o),
+                                  ctypes.c_void_p(bits.data_ptr()),
+                                  ctypes.c_void_p(iters.data_ptr())), "ldpc_decode_rows")
+    return bits, iters
+
+
+def decode_flooding(graph: Graph, llr, max_iter: int, *, want_post: bool = False,
+                    stream=None, workspace=None, **kw):
+    """Flooding-schedule decode of fp32 llr [batch][n_tx] (CUDA): min-sum (algo NORMALISED /
+    OFFSET) or sum-product (algo SUM_PRODUCT).  Returns (bits, iters[, posteriors])."""
+    import torch
+    if not llr.is_cuda or llr.dtype != torch.float32:
+        raise ValueError("llr must be a float32 CUDA tensor")
+    llr = llr.contiguous()
+    B = llr.shape[0]
+    kw.setdefault("n_tx", llr.shape[1])
+    o = make_opts(LLR_FP32, **kw)
+    nb = (graph.K + 7) // 8
+    bits = torch.empty((B, nb), dtype=torch.uint8, device=llr.device)
+    iters = torch.empty((B,), dtype=torch.int32, device=llr.device)
+    post = (torch.empty((B, graph.vars(o.n_rows)), dtype=torch.float32, device=llr.device)
+            if want_post else None)
+    n = int(lib().ldpc_flooding_workspace_floats(graph.handle, B, o.n_rows))
+    if workspace is None or workspace.numel() < n:
+        workspace = torch.empty((max(n, 1),), dtype=torch.float32, device=llr.device)
+    _check(lib().ldpc_decode_flooding(graph.handle, ctypes.c_void_p(llr.data_ptr()), B,
+                                      int(max_iter), _stream_ptr(stream), ctypes.byref(o),
+                                      ctypes.c_void_p(bits.data_ptr()),
+                                      ctypes.c_void_p(iters.data_ptr()),
+                                      None if post is None else ctypes.c_void_p(post.data_ptr()),
+                                      ctypes.c_void_p(workspace.data_ptr())),
+           "ldpc_decode_flooding")
+    return (bits, iters, post) if want_post else (bits, iters)
+
+
 def decode_host(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stream=None,
                 **kw):
     """Decode host LLRs (a CPU tensor or numpy array, pinned memory preferred) through
@@ -235,6 +303,7 @@ def decode_host(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stre
         raise ValueError("decode_host takes host memory")
     llr = llr.contiguous()
     B = llr.shape[0]
+    kw.setdefault("n_tx", llr.shape[1])
     o = make_opts(_llr_type(llr), **kw)
     nb = (graph.K + 7) // 8
     if bits is None:

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(DecodeParams p) {
 
     for (int cw = blockIdx.x; cw < p.batch; cw += gridDim.x) {
         // a0: posteriors from the channel LLRs, zero messages
-        const size_t base = (size_t)cw * p.n_tx;
+        const size_t base = in_row(p, cw) * p.n_tx;
         for (int j = tid; j < N; j += nthr)
             s_Lv[j] = Ar::store((j >= lo && j < hi) ? Ar::from_llr(p.llr, base + (j - lo))
                                                      : Ar::zero());
@@ -211,9 +211,9 @@ __global__ void __launch_bounds__(1024, 1) layered_kernel(DecodeParams p) {
                 const int j = 8 * b + k;
                 if (j < K && Ar::neg(Ar::load(s_Lv[j]))) x |= 1u << k;
             }
-            p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
+            p.bits[out_row(p, cw) * nbytes + b] = (uint8_t)x;
         }
-        if (tid == 0) p.iters[cw] = done;
+        if (tid == 0) p.iters[out_row(p, cw)] = done;
         if (p.post) {
             T *po = reinterpret_cast<T *>(p.post) + (size_t)cw * N;
             for (int j = tid; j < N; j += nthr) po[j] = s_Lv[j];
@@ -267,7 +267,7 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (tmem_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
         return launch_tmem(p, stream);
-    if (rowpair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
+    if (!p.in_rows && !p.out_rows && rowpair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
         return launch_rowpair(p, p.max_deg, stream);
     if (tmem16_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
         return launch_tmem16(p, stream);

@@ -29,7 +29,11 @@
 // iteration (post_iter[t][cw]), and the backward pass then takes one adjoint per iteration
 // (grad_post_iter[t][cw]); the adjoint of iteration t < T-1 is added to gL before the
 // layers of iteration t are undone, so a loss over every iteration's posteriors
-// back-propagates in one sweep.
+// back-propagates in one sweep.  With `detach` the adjoints are reset at every iteration
+// boundary instead (gL = that iteration's own adjoint, G = 0): the parameters of iteration
+// t then receive exactly the partial derivative of iteration t's own loss term, the only
+// term whose inputs do not depend on them through earlier parameters (the full chain
+// grows by orders of magnitude per iteration going backwards).
 #include <cuda_fp16.h>
 
 #include "ldpc_internal.h"
@@ -51,6 +55,7 @@ struct LearnedParams {
     float *grad_llr;         // [batch][n_tx] or null (backward)
     float *post_iter;        // [T][batch][N] or null (forward)
     const float *grad_post_iter;  // [T][batch][N] or null (backward, replaces grad_post)
+    int detach;              // backward: no adjoint flows between iterations
     float *ws;               // workspace
     size_t ws_per_cw;        // floats per codeword
 };
@@ -189,10 +194,16 @@ __global__ void __launch_bounds__(512, 1) learned_bwd_kernel(LearnedParams p) {
             const float *g_t = (p.grad_post_iter && t < p.T - 1)
                                    ? p.grad_post_iter + ((size_t)t * p.batch + cw) * N
                                    : nullptr;
+            const bool reset = p.detach && t < p.T - 1;
             for (int j = tid; j < N; j += nthr) {
                 L[j] = P[(size_t)t * N + j];
-                if (g_t) gL[j] += g_t[j];
+                if (reset)
+                    gL[j] = g_t ? g_t[j] : 0.0f;
+                else if (g_t)
+                    gL[j] += g_t[j];
             }
+            if (reset)
+                for (int k = tid; k < EZ; k += nthr) G[k] = 0.0f;
             __syncthreads();
             const float *c_old = t ? C + (size_t)(t - 1) * EZ : nullptr;
             for (int r = 0; r < n_rows; ++r) {
@@ -285,10 +296,11 @@ size_t learned_ws_floats_per_cw(int N, int EZ, int T) {
 ldpc_status launch_learned(const DecodeParams &dp, int T, const float *params, const float *llr,
                            float *post, const float *grad_post, float *grad_params,
                            float *grad_llr, float *ws, bool backward, cudaStream_t stream,
-                           float *post_iter, const float *grad_post_iter) {
+                           float *post_iter, const float *grad_post_iter, int detach) {
     LearnedParams p;
     p.post_iter = post_iter;
     p.grad_post_iter = grad_post_iter;
+    p.detach = detach;
     p.edges = dp.edges;
     p.row_ptr = dp.row_ptr;
     p.n_rows = dp.n_rows;

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
     uint32_t parity = 0;
     bool failed = false;
     if (pp.use_tma && ht == 0 && cw0 < p.batch)
-        bulk_load(const_cast<int8_t *>(stage), llr_all + (size_t)cw0 * p.n_tx,
+        bulk_load(const_cast<int8_t *>(stage), llr_all + in_row(p, cw0) * p.n_tx,
                   (uint32_t)p.n_tx, bar);
 
     for (int cw = cw0; cw - half < p.batch; cw += stride) {
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                 for (; c + 8 <= pp.ncols; c += 8) tst<8>(tbase + c, z);
                 for (; c < pp.ncols; ++c) tst<1>(tbase + c, z);
             }
-            const int8_t *src = llr_all + (size_t)cw * p.n_tx;
+            const int8_t *src = llr_all + in_row(p, cw) * p.n_tx;
             if (pp.use_tma) {
                 const bool ok = mbar_wait(bar, parity);
                 parity ^= 1u;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                 named_sync(bar_id, nthr_half);
                 // the staging buffer is free: start the copy of this half's next codeword
                 if (pp.use_tma && ht == 0 && cw + stride < p.batch)
-                    bulk_load(const_cast<int8_t *>(stage), llr_all + (size_t)(cw + stride) * p.n_tx,
+                    bulk_load(const_cast<int8_t *>(stage), llr_all + in_row(p, cw + stride) * p.n_tx,
                               (uint32_t)p.n_tx, bar);
 
                 int done = p.max_iter;
@@ -284,9 +284,9 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                         const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
                         if (h < 0x6480u) x |= 1u << kk;
                     }
-                    p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
+                    p.bits[out_row(p, cw) * nbytes + b] = (uint8_t)x;
                 }
-                if (ht == 0) p.iters[cw] = done;
+                if (ht == 0) p.iters[out_row(p, cw)] = done;
                 if (p.post) {
                     int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw * n_cols * Z;
                     for (int c = 0; c < n_cols; ++c)

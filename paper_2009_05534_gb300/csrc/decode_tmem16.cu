@@ -19,7 +19,8 @@
 // thread's messages live in its own TMEM lane, one 32-bit column (two binary16 messages)
 // per edge: a row of degree D is one D-column tcgen05.ld and one tcgen05.st.  A warp reaches
 // only its lane quarter (warp % 4), so the block's warps take column regions of E columns
-// in turn; the allocation is ceil(warps / 4) * E columns rounded up to a power of two.
+// in turn; the allocation is ceil(warps / 4) * E columns rounded up to a power of two, and
+// as many blocks share an SM as its 512 columns hold.
 // When two codewords' regions exceed the 512 columns (BG1-shaped codes at low rate and
 // large Z), a block decodes one codeword: the first 4 * floor(512 / E) warps keep their
 // messages in TMEM and the rest in shared memory ([E][threads] words, one column each).
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
     uint32_t parity = 0;
     bool failed = false;
     if (pp.use_tma && ht == 0 && cw0 < p.batch)
-        bulk_load(const_cast<uint16_t *>(stage), llr_all + (size_t)cw0 * p.n_tx,
+        bulk_load(const_cast<uint16_t *>(stage), llr_all + in_row(p, cw0) * p.n_tx,
                   (uint32_t)(2 * p.n_tx), bar);
 
     for (int cw = cw0; cw - half < p.batch; cw += stride) {
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
             } else {
                 for (int e = 0; e < E; ++e) sm[e * ns] = 0u;
             }
-            const uint16_t *src = llr_all + (size_t)cw * p.n_tx;
+            const uint16_t *src = llr_all + in_row(p, cw) * p.n_tx;
             if (pp.use_tma) {
                 const bool ok = mbar_wait(bar, parity);
                 parity ^= 1u;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
                 named_sync(bar_id, nthr_half);
                 if (pp.use_tma && ht == 0 && cw + stride < p.batch)
                     bulk_load(const_cast<uint16_t *>(stage),
-                              llr_all + (size_t)(cw + stride) * p.n_tx,
+                              llr_all + in_row(p, cw + stride) * p.n_tx,
                               (uint32_t)(2 * p.n_tx), bar);
 
                 int done = p.max_iter;
@@ -308,9 +309,9 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
                         const uint32_t wd = Lb[c * H + i - lane * H];
                         if ((lane ? (wd >> 31) : (wd >> 15)) & 1u) x |= 1u << kk;
                     }
-                    p.bits[(size_t)cw * nbytes + b] = (uint8_t)x;
+                    p.bits[out_row(p, cw) * nbytes + b] = (uint8_t)x;
                 }
-                if (ht == 0) p.iters[cw] = done;
+                if (ht == 0) p.iters[out_row(p, cw)] = done;
                 if (p.post) {
                     uint16_t *po = reinterpret_cast<uint16_t *>(p.post) + (size_t)cw * n_cols * Z;
                     for (int c = 0; c < n_cols; ++c)
@@ -447,23 +448,30 @@ ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream) {
     pp.off_stage = (int)l.off_stage;
     pp.stage_bytes = (int)l.stage_bytes;
     auto kern = sh.cw == 2 ? tmem16_kernel<2> : tmem16_kernel<1>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.total) !=
+    // blocks per SM: as many as shared memory and the 512 TMEM columns allow; the shared
+    // memory request is raised so that no more blocks fit than TMEM can hold (a block
+    // beyond that would only wait in tcgen05.alloc)
+    const int by_tmem = kTmemCols16 / sh.tcols;
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    size_t smem = l.total;
+    const size_t floor_b = (size_t)smem_sm / (by_tmem + 1) + 1024;
+    if (smem < floor_b && floor_b <= (size_t)smem_optin) smem = floor_b;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return LDPC_ERR_CUDA;
     const int threads = sh.cw * sh.wpc * 32;
-    // blocks per SM bounded by TMEM (512 columns per SM) and shared memory
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, l.total) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;
-    const int by_tmem = kTmemCols16 / sh.tcols;
     if (per_sm > by_tmem) per_sm = by_tmem;
     int grid = n_sm * per_sm;
     const int units = (p.batch + sh.cw - 1) / sh.cw;
     if (grid > units) grid = units;
     if (grid < 1) grid = 1;
-    kern<<<grid, threads, l.total, stream>>>(pp);
+    kern<<<grid, threads, smem, stream>>>(pp);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
     return LDPC_OK;

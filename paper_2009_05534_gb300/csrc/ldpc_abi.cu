@@ -160,9 +160,13 @@ int ldpc_graph_vars(ldpc_graph_t h, int n_rows) {
     return (g->K_b + n_rows) * g->Z;
 }
 
-static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int max_iter,
-                                 ldpc_stream_t stream, const ldpc_decode_opts *opts,
-                                 uint8_t *bits, int32_t *iters, void *post, void *c2v) {
+// Validates the arguments of a batch decode and fills the kernel parameters; *empty is
+// set for a zero batch (nothing to launch).  flooding: the flooding decoder's rules.
+static ldpc_status decode_params(ldpc_graph_t h, const void *llr, int batch, int max_iter,
+                                 const ldpc_decode_opts *opts, uint8_t *bits, int32_t *iters,
+                                 void *post, void *c2v, bool flooding, ldpc::DecodeParams *out,
+                                 ldpc_decode_opts *o_out, bool *empty) {
+    *empty = false;
     if (!h) return LDPC_ERR_INVALID_ARG;
     Graph *g = reinterpret_cast<Graph *>(h);
     ldpc_decode_opts o;
@@ -172,7 +176,12 @@ static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int
         ldpc_decode_opts_default(&o);
     if (batch < 0 || max_iter < 1 || max_iter > ldpc::kMaxIter) return LDPC_ERR_INVALID_ARG;
     if (o.llr_type < LDPC_LLR_INT8 || o.llr_type > LDPC_LLR_FP32) return LDPC_ERR_INVALID_ARG;
-    if (o.algo < LDPC_NORMALISED || o.algo > LDPC_LEARNED) return LDPC_ERR_INVALID_ARG;
+    if (o.algo < LDPC_NORMALISED || o.algo > LDPC_SUM_PRODUCT) return LDPC_ERR_INVALID_ARG;
+    if (flooding) {
+        if (o.llr_type != LDPC_LLR_FP32 || o.algo == LDPC_LEARNED) return LDPC_ERR_UNSUPPORTED;
+    } else if (o.algo == LDPC_SUM_PRODUCT) {
+        return LDPC_ERR_UNSUPPORTED;
+    }
     if (o.llr_type == LDPC_LLR_INT8 && o.algo != LDPC_OFFSET) return LDPC_ERR_UNSUPPORTED;
     if (o.algo == LDPC_LEARNED && !o.learned_params) return LDPC_ERR_INVALID_ARG;
     if (o.cluster_size != 1) return LDPC_ERR_UNSUPPORTED;
@@ -185,13 +194,16 @@ static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int
     if (o.punct_cols < 0 || o.punct_cols > n_cols) return LDPC_ERR_INVALID_ARG;
     const int n_tx = o.n_tx == 0 ? (n_cols - o.punct_cols) * g->Z : o.n_tx;
     if (n_tx < 0 || o.punct_cols * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
-    if (batch == 0) return LDPC_OK;
+    if (batch == 0) {
+        *empty = true;
+        return LDPC_OK;
+    }
     if (!llr || !bits || !iters) return LDPC_ERR_INVALID_ARG;
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != g->device) return LDPC_ERR_INVALID_ARG;
 
-    ldpc::DecodeParams p;
+    ldpc::DecodeParams &p = *out;
     p.edges = g->d_edges;
     p.row_ptr = g->d_row_ptr;
     p.h_edges = g->h_edges;
@@ -218,6 +230,21 @@ static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int
     p.post = post;
     p.c2v = c2v;
     p.status = g->d_status;
+    p.in_rows = nullptr;
+    p.out_rows = nullptr;
+    *o_out = o;
+    return LDPC_OK;
+}
+
+static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int max_iter,
+                                 ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                                 uint8_t *bits, int32_t *iters, void *post, void *c2v) {
+    ldpc::DecodeParams p;
+    ldpc_decode_opts o;
+    bool empty = false;
+    const ldpc_status st = decode_params(h, llr, batch, max_iter, opts, bits, iters, post, c2v,
+                                         false, &p, &o, &empty);
+    if (st != LDPC_OK || empty) return st;
     return ldpc::launch_layered(p, o.llr_type, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -226,6 +253,22 @@ ldpc_status ldpc_decode(ldpc_graph_t g, const void *llr_dev, int batch, int max_
                         uint8_t *hard_bits_dev, int32_t *iters_dev) {
     return decode_common(g, llr_dev, batch, max_iter, stream, opts, hard_bits_dev, iters_dev,
                          nullptr, nullptr);
+}
+
+ldpc_status ldpc_decode_rows(ldpc_graph_t g, const void *llr_dev, const int32_t *in_rows_dev,
+                             const int32_t *out_rows_dev, int batch, int max_iter,
+                             ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                             uint8_t *hard_bits_dev, int32_t *iters_dev) {
+    ldpc::DecodeParams p;
+    ldpc_decode_opts o;
+    bool empty = false;
+    const ldpc_status st = decode_params(g, llr_dev, batch, max_iter, opts, hard_bits_dev,
+                                         iters_dev, nullptr, nullptr, false, &p, &o, &empty);
+    if (st != LDPC_OK || empty) return st;
+    if (!in_rows_dev || !out_rows_dev) return LDPC_ERR_INVALID_ARG;
+    p.in_rows = in_rows_dev;
+    p.out_rows = out_rows_dev;
+    return ldpc::launch_layered(p, o.llr_type, reinterpret_cast<cudaStream_t>(stream));
 }
 
 ldpc_status ldpc_decode_debug(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
@@ -545,7 +588,7 @@ ldpc_status ldpc_learned_forward_iter(ldpc_graph_t h, const float *llr, int batc
 ldpc_status ldpc_learned_backward_iter(ldpc_graph_t h, const float *grad_post_iter, int batch,
                                        int T, int n_rows, int n_tx, const float *params,
                                        ldpc_stream_t stream, float *ws, float *grad_params,
-                                       float *grad_llr) {
+                                       float *grad_llr, int detach) {
     ldpc::DecodeParams p;
     ldpc_status st = learned_common(h, batch, T, n_rows, n_tx, &p);
     if (st != LDPC_OK) return st;
@@ -553,7 +596,28 @@ ldpc_status ldpc_learned_backward_iter(ldpc_graph_t h, const float *grad_post_it
     if (!grad_post_iter || !params || !ws || !grad_params) return LDPC_ERR_INVALID_ARG;
     return ldpc::launch_learned(p, T, params, nullptr, nullptr, nullptr, grad_params, grad_llr,
                                 ws, true, reinterpret_cast<cudaStream_t>(stream), nullptr,
-                                grad_post_iter);
+                                grad_post_iter, detach ? 1 : 0);
+}
+
+size_t ldpc_flooding_workspace_floats(ldpc_graph_t h, int batch, int n_rows) {
+    if (!h || batch < 0) return 0;
+    Graph *g = reinterpret_cast<Graph *>(h);
+    const int r = n_rows == 0 ? g->M_bg : n_rows;
+    if (r < 1 || r > g->M_bg) return 0;
+    return (size_t)batch * ldpc::flooding_ws_floats_per_cw(g->row_ptr[r], g->Z);
+}
+
+ldpc_status ldpc_decode_flooding(ldpc_graph_t h, const float *llr, int batch, int max_iter,
+                                 ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                                 uint8_t *bits, int32_t *iters, float *post, float *ws) {
+    ldpc::DecodeParams p;
+    ldpc_decode_opts o;
+    bool empty = false;
+    const ldpc_status st = decode_params(h, llr, batch, max_iter, opts, bits, iters, post,
+                                         nullptr, true, &p, &o, &empty);
+    if (st != LDPC_OK || empty) return st;
+    if (!ws) return LDPC_ERR_INVALID_ARG;
+    return ldpc::launch_flooding(p, ws, reinterpret_cast<cudaStream_t>(stream));
 }
 
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t h, ldpc_stream_t stream) {

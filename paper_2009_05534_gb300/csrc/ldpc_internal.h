@@ -53,7 +53,17 @@ struct DecodeParams {
     void *post;               // [batch][n_cols * Z] or null
     void *c2v;                // [batch][E * Z] or null
     int *status;              // device status word
+    const int32_t *in_rows;   // [batch] LLR row of codeword b, or null (row b)
+    const int32_t *out_rows;  // [batch] output row of codeword b, or null (row b)
 };
+
+// source and destination rows of codeword b of a batch (identity without row maps)
+__host__ __device__ __forceinline__ size_t in_row(const DecodeParams &p, int b) {
+    return (size_t)(p.in_rows ? p.in_rows[b] : b);
+}
+__host__ __device__ __forceinline__ size_t out_row(const DecodeParams &p, int b) {
+    return (size_t)(p.out_rows ? p.out_rows[b] : b);
+}
 
 // One codeword of a work list (device side; built by ldpc_decode_list).
 struct ListItem {
@@ -84,12 +94,18 @@ ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stre
 bool tmem16_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream);
 
+// Flooding-schedule decoder, fp32 min-sum or sum-product (decode_flooding.cu); ws holds
+// the messages of every codeword.
+size_t flooding_ws_floats_per_cw(int E, int Z);
+ldpc_status launch_flooding(const DecodeParams &p, float *ws, cudaStream_t stream);
+
 // Learned min-sum forward / backward (decode_learned.cu); ws holds the checkpoints.
 size_t learned_ws_floats_per_cw(int N, int EZ, int T);
 ldpc_status launch_learned(const DecodeParams &dp, int T, const float *params, const float *llr,
                            float *post, const float *grad_post, float *grad_params,
                            float *grad_llr, float *ws, bool backward, cudaStream_t stream,
-                           float *post_iter = nullptr, const float *grad_post_iter = nullptr);
+                           float *post_iter = nullptr, const float *grad_post_iter = nullptr,
+                           int detach = 0);
 
 // Work-list decode (decode_rowpair.cu): items are taken dynamically through *d_counter,
 // which must be zero at launch.

@@ -39,7 +39,7 @@ def _bind():
     L.ldpc_learned_backward.restype = _I
     L.ldpc_learned_forward_iter.argtypes = [_P, _P, _I, _I, _I, _I, _P, _P, _P, _P]
     L.ldpc_learned_forward_iter.restype = _I
-    L.ldpc_learned_backward_iter.argtypes = [_P, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P]
+    L.ldpc_learned_backward_iter.argtypes = [_P, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _I]
     L.ldpc_learned_backward_iter.restype = _I
     L._learned_bound = True
     return L
@@ -108,8 +108,11 @@ def forward_iter(graph: Graph, llr, params, *, n_rows: int = 0, n_tx: int = 0, w
 
 
 def backward_iter(graph: Graph, grad_post_iter, params, ws, *, n_tx: int, n_rows: int = 0,
-                  want_grad_llr: bool = False, stream=None):
-    """Gradients of a loss over every iteration's posteriors (adjoints [T][batch][N])."""
+                  want_grad_llr: bool = False, stream=None, detach: bool = False):
+    """Gradients of a loss over every iteration's posteriors (adjoints [T][batch][N]).
+
+    detach: no adjoint flows between iterations, so iteration t's parameters get the
+    partial derivative of iteration t's own loss term only."""
     import torch
     L = _bind()
     g = grad_post_iter.contiguous().float()
@@ -118,7 +121,8 @@ def backward_iter(graph: Graph, grad_post_iter, params, ws, *, n_tx: int, n_rows
     gp = torch.empty((B,) + tuple(params.shape), dtype=torch.float32, device=g.device)
     gl = torch.empty((B, n_tx), dtype=torch.float32, device=g.device) if want_grad_llr else None
     _check(L.ldpc_learned_backward_iter(graph.handle, _vp(g), B, T, n_rows, n_tx, _vp(params),
-                                        _stream_ptr(stream), _vp(ws), _vp(gp), _vp(gl)),
+                                        _stream_ptr(stream), _vp(ws), _vp(gp), _vp(gl),
+                                        int(detach)),
            "ldpc_learned_backward_iter")
     return gp, gl
 
@@ -143,9 +147,9 @@ def _autograd():
 
     class LearnedDecodeIterFn(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, params, llr, graph, n_rows, n_tx):
+        def forward(ctx, params, llr, graph, n_rows, n_tx, detach):
             post, ws = forward_iter(graph, llr, params, n_rows=n_rows, n_tx=n_tx)
-            ctx.graph, ctx.n_rows, ctx.n_tx = graph, n_rows, llr.shape[1]
+            ctx.graph, ctx.n_rows, ctx.n_tx, ctx.detach = graph, n_rows, llr.shape[1], detach
             ctx.save_for_backward(params, ws)
             return post
 
@@ -153,8 +157,9 @@ def _autograd():
         def backward(ctx, grad_post):
             params, ws = ctx.saved_tensors
             gp, gl = backward_iter(ctx.graph, grad_post, params, ws, n_tx=ctx.n_tx,
-                                   n_rows=ctx.n_rows, want_grad_llr=ctx.needs_input_grad[1])
-            return gp.sum(0), gl, None, None, None
+                                   n_rows=ctx.n_rows, want_grad_llr=ctx.needs_input_grad[1],
+                                   detach=ctx.detach)
+            return gp.sum(0), gl, None, None, None, None
 
     return LearnedDecodeFn, LearnedDecodeIterFn
 
@@ -163,14 +168,16 @@ _FN = None
 
 
 def learned_decode(params, llr, graph: Graph, n_rows: int = 0, n_tx: int = 0,
-                   every_iteration: bool = False):
+                   every_iteration: bool = False, detach: bool = False):
     """Differentiable learned decode: posteriors = f(params, llr) [batch][N], or with
-    every_iteration the posteriors after each iteration [T][batch][N]."""
+    every_iteration the posteriors after each iteration [T][batch][N] (detach: gradients
+    do not flow between iterations)."""
     global _FN
     if _FN is None:
         _FN = _autograd()
-    fn = _FN[1] if every_iteration else _FN[0]
-    return fn.apply(params, llr, graph, n_rows, n_tx)
+    if every_iteration:
+        return _FN[1].apply(params, llr, graph, n_rows, n_tx, bool(detach))
+    return _FN[0].apply(params, llr, graph, n_rows, n_tx)
 
 
 def bce_loss(post, codewords, iter_weights=None):
@@ -209,11 +216,12 @@ def load_checkpoint(path):
 
 def train(graph: Graph, n_rows: int, T: int, batches, *, lr: float = 1e-3, params=None,
           log_every: int = 0, n_steps: int | None = None, checkpoint=None,
-          checkpoint_every: int = 0, iter_weights=None):
+          checkpoint_every: int = 0, iter_weights=None, detach: bool = False):
     """Adam on the BCE loss.  Returns (params, loss history).
 
     iter_weights ([T] or None): None trains on the final posteriors; otherwise the loss is
-    the weighted sum of the BCE after every iteration.
+    the weighted sum of the BCE after every iteration, and with detach each iteration's
+    parameters follow only their own iteration's term.
 
     batches: an iterable of (llr float CUDA [B][n_tx], codeword bits CUDA [B][N]) pairs, or a
     callable k -> pair for steps k = 0 .. n_steps-1.  With a checkpoint path, an existing
@@ -247,7 +255,8 @@ def train(graph: Graph, n_rows: int, T: int, batches, *, lr: float = 1e-3, param
     k = start
     for llr, cw in stream:
         opt.zero_grad(set_to_none=True)
-        post = learned_decode(p, llr, graph, n_rows, llr.shape[1], every_iteration=w is not None)
+        post = learned_decode(p, llr, graph, n_rows, llr.shape[1], every_iteration=w is not None,
+                              detach=detach)
         loss = bce_loss(post, cw, w)
         loss.backward()
         opt.step()

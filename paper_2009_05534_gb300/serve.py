@@ -126,16 +126,32 @@ def latency_stats(lat) -> dict:
             "p99_us": float(np.percentile(lat, 99)), "max_us": float(lat.max())}
 
 
+@dataclass
+class LearnedClass:
+    """Requests served by the learned decoder: one graph and (beta, gamma) table, their
+    binary16 LLRs in a device pool; request id i uses pool row pick[i] (-1: plain request).
+    """
+    graph: object
+    pool: object               # CUDA float16 [rows][n_tx]
+    table: object              # CUDA float32 [T][n_rows][2]
+    pick: np.ndarray           # int32 per request id
+    max_iter: int
+    n_rows: int = 0
+
+
 class GpuBackend:
     """Device backend: output arena, round-robin streams, one work-list launch per slot.
 
     table: numpy record array (``work_item_dtype``), one row per request id, with graph,
     LLR pointer, n_rows, n_tx and max_iter filled in; the output pointers are set at
-    admission from the arena.  ks: information bits per request id.
+    admission from the arena.  ks: information bits per request id.  learned: optional
+    LearnedClass; its requests of a slot are decoded by one row-mapped learned decode
+    (`ldpc_decode_rows`) on the same stream, into an arena of their own.
     """
 
     def __init__(self, table: np.ndarray, ks: np.ndarray, n_buffers: int, kmax: int,
-                 n_streams: int = 4, early_stop: bool = True, keep_results: bool = False):
+                 n_streams: int = 4, early_stop: bool = True, keep_results: bool = False,
+                 learned: LearnedClass | None = None):
         import torch
 
         import paper_2009_05534_gb300 as ldpc
@@ -152,6 +168,11 @@ class GpuBackend:
         self.k = 0
         self.keep = keep_results
         self.results: dict = {}
+        self.learned = learned
+        if learned is not None:
+            self.nb_l = (learned.graph.K + 7) // 8
+            self.bits_l = torch.zeros((n_buffers, self.nb_l), dtype=torch.uint8, device="cuda")
+            self.iters_l = torch.zeros((n_buffers,), dtype=torch.int32, device="cuda")
 
     def capacity(self):
         return self.n
@@ -162,10 +183,25 @@ class GpuBackend:
         self.k += 1
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(self.clock)
-        items = self.table[ids].copy()
-        items["hard_bits"] = self.bits.data_ptr() + outs * self.nb
-        items["iters"] = self.iters.data_ptr() + outs * 4
-        self.ldpc.decode_list_array(items, stream=s, early_stop=self.early_stop)
+        lc = self.learned
+        if lc is not None:
+            sel = lc.pick[ids] >= 0
+            ids_p, outs_p = ids[~sel], outs[~sel]
+        else:
+            ids_p, outs_p = ids, outs
+        if len(ids_p):
+            items = self.table[ids_p].copy()
+            items["hard_bits"] = self.bits.data_ptr() + outs_p * self.nb
+            items["iters"] = self.iters.data_ptr() + outs_p * 4
+            self.ldpc.decode_list_array(items, stream=s, early_stop=self.early_stop)
+        if lc is not None and sel.any():
+            rows = np.stack([lc.pick[ids[sel]], outs[sel]]).astype(np.int32)
+            with torch.cuda.stream(s):
+                dev = torch.from_numpy(rows).to("cuda", non_blocking=False)
+            self.ldpc.decode_rows(lc.graph, lc.pool, dev[0], dev[1], lc.max_iter,
+                                  bits=self.bits_l, iters=self.iters_l, stream=s,
+                                  algo=self.ldpc.LEARNED, learned=lc.table,
+                                  n_rows=lc.n_rows, early_stop=self.early_stop)
         end.record(s)
         return (start, end)
 
@@ -181,7 +217,13 @@ class GpuBackend:
             o = self.torch.from_numpy(outs).cuda()
             its = self.iters[o].cpu().numpy()
             bits = self.bits[o].cpu().numpy()
-            for i, it, b in zip(ids.tolist(), its, bits):
+            if self.learned is not None:
+                its_l = self.iters_l[o].cpu().numpy()
+                bits_l = self.bits_l[o].cpu().numpy()
+                is_l = self.learned.pick[ids] >= 0
+            for k, (i, it, b) in enumerate(zip(ids.tolist(), its, bits)):
+                if self.learned is not None and is_l[k]:
+                    b, it = bits_l[k], its_l[k]
                 self.results[i] = (b[: (int(self.ks[i]) + 7) // 8].copy(), int(it))
         return start.elapsed_time(end) * 1e3
 

@@ -70,7 +70,7 @@ def training_set(kind: str, Z: int, n_cw: int, batch: int, ebn0_lo: float, ebn0_
 
 def train_table(graph: Graph, n_rows: int, T: int, llr, cw, *, batch: int, epochs: int,
                 lr: float, seed: int, checkpoint=None, log_every: int = 0,
-                every_iteration: bool = True):
+                every_iteration: bool = True, detach: bool = False):
     """Adam over `epochs` seeded shuffles of the device-resident training set; the loss is
     the mean over iterations of the BCE after each iteration (or the final BCE only)."""
     import torch
@@ -87,7 +87,7 @@ def train_table(graph: Graph, n_rows: int, T: int, llr, cw, *, batch: int, epoch
     w = np.full(T, 1.0 / T) if every_iteration else None
     return _learned.train(graph, n_rows, T, batch_fn, n_steps=per_epoch * epochs, lr=lr,
                           checkpoint=checkpoint, checkpoint_every=64, log_every=log_every,
-                          iter_weights=w)
+                          iter_weights=w, detach=detach)
 
 
 def bler_sweep(graph: Graph, kind: str, Z: int, T: int, tables: dict, ebn0s, n_cw: int,
@@ -171,6 +171,9 @@ def main(argv=None):
     ap.add_argument("--eval-grid", default="1.5:4.5:0.25")
     ap.add_argument("--loss", choices=("every", "final"), default="every",
                     help="BCE after every iteration (mean) or of the final posteriors only")
+    ap.add_argument("--grad", choices=("local", "full"), default="local",
+                    help="with --loss every: each iteration's parameters follow their own "
+                         "term (local) or the whole unrolled chain (full)")
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
@@ -187,7 +190,8 @@ def main(argv=None):
     t1 = time.time()
     table, hist = train_table(graph, n_rows, a.T, llr, cw, batch=a.batch, epochs=a.epochs,
                               lr=a.lr, seed=a.seed, checkpoint=a.checkpoint, log_every=32,
-                              every_iteration=a.loss == "every")
+                              every_iteration=a.loss == "every",
+                              detach=a.loss == "every" and a.grad == "local")
     torch.cuda.synchronize()
     t_train = time.time() - t1
     del llr, cw
@@ -205,6 +209,10 @@ def main(argv=None):
                      "steps": len(hist), "optimizer": "Adam", "lr": a.lr,
                      "loss": ("mean over iterations of the BCE after each iteration"
                               if a.loss == "every" else "BCE of the final posteriors"),
+                     "gradient": ("per-iteration partial derivatives (adjoints reset at "
+                                  "iteration boundaries)"
+                                  if a.loss == "every" and a.grad == "local"
+                                  else "full reverse mode through the unrolled iterations"),
                      "ebn0_db": [a.ebn0_lo, a.ebn0_hi], "modulation": "QPSK",
                      "seed": a.seed, "llr_storage": "binary16",
                      "loss_first": float(hist[0]), "loss_last": float(hist[-1]),

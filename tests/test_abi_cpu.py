@@ -68,3 +68,17 @@ def test_invalid_args_rejected_on_host(L):
     assert L.ldpc_decode(None, None, 1, 10, None, None, None, None) == 1
     assert L.ldpc_graph_edges(None, 0) == -1
     assert L.ldpc_graph_destroy(None) == 1
+
+
+def test_flooding_and_learned_entry_points_reject_null_graph(L):
+    L.ldpc_flooding_workspace_floats.restype = ctypes.c_size_t
+    L.ldpc_flooding_workspace_floats.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    assert L.ldpc_flooding_workspace_floats(None, 4, 0) == 0
+    assert L.ldpc_decode_flooding(None, None, 1, 10, None, None, None, None, None, None) == 1
+    L.ldpc_learned_workspace_floats.restype = ctypes.c_size_t
+    L.ldpc_learned_workspace_floats.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int]
+    assert L.ldpc_learned_workspace_floats(None, 4, 10, 0) == 0
+    assert L.ldpc_learned_forward_iter(None, None, 1, 10, 0, 0, None, None, None, None) == 1
+    assert L.ldpc_learned_backward_iter(None, None, 1, 10, 0, 0, None, None, None, None, None,
+                                        0) == 1

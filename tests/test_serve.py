@@ -114,3 +114,68 @@ def test_results_same_alone_and_in_mix():
     assert (sch.completed_latencies() > 0).all()
     for g in graphs.values():
         g.close()
+
+
+@pytest.mark.gpu
+def test_learned_and_plain_served_together():
+    """Learned requests (binary16, BG2-shaped Z=128, a (beta, gamma) table) share slots with
+    plain int8 requests; each result equals the same codeword decoded alone."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from fractions import Fraction
+
+    from paper_2009_05534_gb300 import build
+    build.build()
+    import paper_2009_05534_gb300 as ldpc
+    from paper_2009_05534_gb300.serve import GpuBackend, LearnedClass
+    from synth import make_workload
+    rng = np.random.default_rng(4)
+    T = 8
+    wl_l = make_workload("BG2", 128, 24, 2.5, seed=900, graph_seed=0)
+    g_l = ldpc.Graph(wl_l.base, wl_l.K_b, 128)
+    pool = torch.from_numpy(wl_l.llr_fp16()).cuda()
+    tab = np.zeros((T, wl_l.n_rows, 2), np.float32)
+    tab[..., 0] = rng.uniform(0.4, 0.9, size=(T, wl_l.n_rows))
+    tab[..., 1] = rng.uniform(0.0, 0.3, size=(T, wl_l.n_rows))
+    tab_d = torch.from_numpy(tab).cuda()
+    graphs, llrs = {}, []
+    n = 48
+    table = np.zeros(n, dtype=ldpc.work_item_dtype)
+    ks = np.zeros(n, np.int64)
+    pick = np.full(n, -1, np.int32)
+    alone = []
+    for i in range(n):
+        if rng.integers(3) == 0:                               # learned request
+            pick[i] = int(rng.integers(len(pool)))
+            ks[i] = wl_l.K
+            b, it = ldpc.decode(g_l, pool[pick[i]][None, :], T, algo=ldpc.LEARNED,
+                                learned=tab_d)
+            torch.cuda.synchronize()
+            alone.append((b.cpu().numpy()[0], int(it.item())))
+            continue
+        Z = int(rng.choice([64, 128, 384]))
+        wl = make_workload("BG1", Z, 1, 2.0, rate=Fraction(1, 2), seed=700 + i, graph_seed=0)
+        if Z not in graphs:
+            graphs[Z] = ldpc.Graph(wl.base, wl.K_b, Z)
+        llr = torch.from_numpy(wl.llr_int8()[0]).cuda()
+        llrs.append(llr)
+        table[i] = (graphs[Z].handle.value, llr.data_ptr(), 0, 0, wl.n_rows, wl.n_tx, T)
+        ks[i] = wl.K
+        b, it = ldpc.decode(graphs[Z], llr[None, :], T, n_rows=wl.n_rows, n_tx=wl.n_tx)
+        torch.cuda.synchronize()
+        alone.append((b.cpu().numpy()[0], int(it.item())))
+    assert (pick >= 0).sum() >= 8 and (pick < 0).sum() >= 8
+    kmax = max([g.K for g in graphs.values()] + [g_l.K])
+    be = GpuBackend(table, ks, n_buffers=12, kmax=kmax, n_streams=2, keep_results=True,
+                    learned=LearnedClass(g_l, pool, tab_d, pick, T))
+    sch = SlotScheduler(be, slot_us=500.0)
+    for s in range(0, n, 5):
+        sch.submit(min(5, n - s))
+        sch.step()
+    sch.drain()
+    assert len(be.results) == n
+    for i, (b, it) in be.results.items():
+        assert np.array_equal(b, alone[i][0]) and it == alone[i][1], i
+    for g in list(graphs.values()) + [g_l]:
+        g.close()
