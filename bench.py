@@ -48,6 +48,8 @@ def parse():
                     help="skip the rate-8/9 QAM int8-vs-binary16 measurement")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip the learned-vs-plain BLER and throughput measurement")
+    ap.add_argument("--no-flooding", dest="flooding", action="store_false",
+                    help="skip the flooding-schedule comparison")
     return ap.parse_args()
 
 
@@ -349,6 +351,49 @@ def high_load_measure(batch: int = 8192, caps=(5, 10, 20), reps: int = 5, seed: 
             "points": out}
 
 
+# ------------------------------------------------------------ flooding baseline (Sec. V)
+
+def flooding_measure(wl, graph, q_dev, batch: int = 512, reps: int = 3):
+    """The paper's comparison schedule on the headline codewords: flooding min-sum
+    (normalised 0.75, fp32) and sum-product with a cap of 2T = 20 iterations against the
+    layered int8 decoder with a cap of T = 10, all stopping at a valid codeword: Gbit/s,
+    BLER and mean iterations of each on the same codewords."""
+    import torch
+
+    import paper_2009_05534_gb300 as ldpc
+    stream = torch.cuda.Stream()
+    llr = torch.from_numpy(wl.llr[:batch]).cuda()
+    info = wl.info[:batch]
+    out = {"batch": batch}
+    ws = torch.empty((int(ldpc.lib().ldpc_flooding_workspace_floats(graph.handle, batch, 0)),),
+                     dtype=torch.float32, device="cuda")
+    for name, algo, T in (("flooding_min_sum", ldpc.NORMALISED, 2 * T_ITER),
+                          ("flooding_sum_product", ldpc.SUM_PRODUCT, 2 * T_ITER)):
+        res = {}
+
+        def run(k):
+            res["o"] = ldpc.decode_flooding(graph, llr, T, algo=algo, alpha=0.75,
+                                            early_stop=True, stream=stream, workspace=ws)
+
+        run(0)
+        sec = _timed(run, reps, stream)
+        bits = ldpc.unpack_bits(res["o"][0].cpu().numpy(), wl.K)
+        out[name] = {"max_iter": T, "gbps": batch * wl.K / sec / 1e9,
+                     "bler": float((bits != info).any(1).mean()),
+                     "mean_iterations": float(res["o"][1].float().mean())}
+
+    def run_l(k):
+        res["l"] = ldpc.decode(graph, q_dev[:batch], T_ITER, early_stop=True, stream=stream)
+
+    run_l(0)
+    sec = _timed(run_l, reps, stream)
+    bits = ldpc.unpack_bits(res["l"][0].cpu().numpy(), wl.K)
+    out["layered_int8"] = {"max_iter": T_ITER, "gbps": batch * wl.K / sec / 1e9,
+                           "bler": float((bits != info).any(1).mean()),
+                           "mean_iterations": float(res["l"][1].float().mean())}
+    return out
+
+
 # -------------------------------------------------------- learned vs plain (BG2, Z = 128)
 
 LEARNED_TABLE = "learned_bg2_z128_t10.json"
@@ -570,6 +615,7 @@ def run_ours(args):
 
     serving = serving_measure(args.serve_slots) if args.serve_slots > 0 else None
     latency = latency_measure(wl, graph)
+    flooding = flooding_measure(wl, graph, bufs[0]) if args.flooding else None
     high_load = high_load_measure() if args.high_load else None
     learned = learned_measure() if args.learned else None
 
@@ -605,6 +651,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": B * (nbytes + 4)},
             "serving": serving,
             "latency": latency,
+            "flooding": flooding,
             "high_load": high_load,
             "learned": learned,
             "gpu_launches": launches,

@@ -237,9 +237,11 @@ def decode(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stream=No
 
 
 def decode_rows(graph: Graph, llr, in_rows, out_rows, max_iter: int, *, bits, iters,
-                stream=None, **kw):
+                stream=None, check_rows: bool = True, **kw):
     """Decode codewords llr[in_rows[b]] (a CUDA pool [rows][n_tx]) into bits[out_rows[b]] and
-    iters[out_rows[b]]; in_rows / out_rows are int32 CUDA tensors of the batch length."""
+    iters[out_rows[b]]; in_rows / out_rows are int32 CUDA tensors of the batch length.
+    check_rows reads the maps back to validate them (a device sync); a caller that built
+    them from validated indices passes False."""
     import torch
     if not (llr.is_cuda and in_rows.is_cuda and out_rows.is_cuda):
         raise ValueError("llr and the row maps must be CUDA tensors")
@@ -248,8 +250,9 @@ def decode_rows(graph: Graph, llr, in_rows, out_rows, max_iter: int, *, bits, it
     n = in_rows.numel()
     if out_rows.numel() != n:
         raise ValueError("row maps differ in length")
-    if n and (int(in_rows.max()) >= llr.shape[0] or int(out_rows.max()) >= bits.shape[0]
-              or int(in_rows.min()) < 0 or int(out_rows.min()) < 0):
+    if check_rows and n and (int(in_rows.max()) >= llr.shape[0] or
+                             int(out_rows.max()) >= bits.shape[0] or
+                             int(in_rows.min()) < 0 or int(out_rows.min()) < 0):
         raise ValueError("row map outside the buffers")
     llr = llr.contiguous()
     kw.setdefault("n_tx", llr.shape[1])

@@ -173,6 +173,15 @@ class GpuBackend:
             self.nb_l = (learned.graph.K + 7) // 8
             self.bits_l = torch.zeros((n_buffers, self.nb_l), dtype=torch.uint8, device="cuda")
             self.iters_l = torch.zeros((n_buffers,), dtype=torch.int32, device="cuda")
+            # learned batches run on streams of their own, concurrently with the slot's
+            # work-list launch; their row maps go up from a pinned ring (a pageable copy
+            # would stall the host until the stream drains)
+            self.lstreams = [torch.cuda.Stream() for _ in range(n_streams)]
+            self.ring = 64
+            self.rows_pin = torch.zeros((self.ring, 2, n_buffers), dtype=torch.int32).pin_memory()
+            self.rows_dev = torch.zeros((self.ring, 2, n_buffers), dtype=torch.int32,
+                                        device="cuda")
+            self.ring_ev = [None] * self.ring
 
     def capacity(self):
         return self.n
@@ -194,25 +203,42 @@ class GpuBackend:
             items["hard_bits"] = self.bits.data_ptr() + outs_p * self.nb
             items["iters"] = self.iters.data_ptr() + outs_p * 4
             self.ldpc.decode_list_array(items, stream=s, early_stop=self.early_stop)
-        if lc is not None and sel.any():
-            rows = np.stack([lc.pick[ids[sel]], outs[sel]]).astype(np.int32)
-            with torch.cuda.stream(s):
-                dev = torch.from_numpy(rows).to("cuda", non_blocking=False)
-            self.ldpc.decode_rows(lc.graph, lc.pool, dev[0], dev[1], lc.max_iter,
-                                  bits=self.bits_l, iters=self.iters_l, stream=s,
-                                  algo=self.ldpc.LEARNED, learned=lc.table,
-                                  n_rows=lc.n_rows, early_stop=self.early_stop)
         end.record(s)
-        return (start, end)
+        end_l = None
+        if lc is not None and sel.any():
+            sl = self.lstreams[(self.k - 1) % len(self.lstreams)]
+            r = (self.k - 1) % self.ring
+            if self.ring_ev[r] is not None:
+                self.ring_ev[r].synchronize()          # the copy that last used slot r
+            n = int(sel.sum())
+            pin = self.rows_pin[r].numpy()
+            pin[0, :n] = lc.pick[ids[sel]]
+            pin[1, :n] = outs[sel]
+            dev = self.rows_dev[r]
+            with torch.cuda.stream(sl):
+                dev[:, :n].copy_(self.rows_pin[r][:, :n], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(sl)
+            self.ring_ev[r] = ev
+            self.ldpc.decode_rows(lc.graph, lc.pool, dev[0, :n], dev[1, :n], lc.max_iter,
+                                  bits=self.bits_l, iters=self.iters_l, stream=sl,
+                                  algo=self.ldpc.LEARNED, learned=lc.table,
+                                  n_rows=lc.n_rows, early_stop=self.early_stop,
+                                  check_rows=False)
+            end_l = torch.cuda.Event(enable_timing=True)
+            end_l.record(sl)
+        return (start, end, end_l)
 
     def done(self, handle):
-        return handle[1].query()
+        return handle[1].query() and (handle[2] is None or handle[2].query())
 
     def wait(self, handle):
         handle[1].synchronize()
+        if handle[2] is not None:
+            handle[2].synchronize()
 
     def finish(self, handle, ids, outs):
-        start, end = handle
+        start, end, end_l = handle
         if self.keep:
             o = self.torch.from_numpy(outs).cuda()
             its = self.iters[o].cpu().numpy()
@@ -225,7 +251,10 @@ class GpuBackend:
                 if self.learned is not None and is_l[k]:
                     b, it = bits_l[k], its_l[k]
                 self.results[i] = (b[: (int(self.ks[i]) + 7) // 8].copy(), int(it))
-        return start.elapsed_time(end) * 1e3
+        t = start.elapsed_time(end)
+        if end_l is not None:
+            t = max(t, start.elapsed_time(end_l))
+        return t * 1e3
 
 
 def run_paced(scheduler: SlotScheduler, counts, slot_us: float = 500.0) -> float:
