@@ -50,6 +50,8 @@ def parse():
                     help="skip the learned-vs-plain BLER and throughput measurement")
     ap.add_argument("--no-flooding", dest="flooding", action="store_false",
                     help="skip the flooding-schedule comparison")
+    ap.add_argument("--no-latency", dest="latency", action="store_false",
+                    help="skip the single-codeword latency measurement")
     return ap.parse_args()
 
 
@@ -614,7 +616,7 @@ def run_ours(args):
     traffic = profiled_traffic("layered_int8_bg1_z384")
 
     serving = serving_measure(args.serve_slots) if args.serve_slots > 0 else None
-    latency = latency_measure(wl, graph)
+    latency = latency_measure(wl, graph) if args.latency else None
     flooding = flooding_measure(wl, graph, bufs[0]) if args.flooding else None
     high_load = high_load_measure() if args.high_load else None
     learned = learned_measure() if args.learned else None
