@@ -52,12 +52,32 @@ def parse():
                     help="skip the flooding-schedule comparison")
     ap.add_argument("--no-latency", dest="latency", action="store_false",
                     help="skip the single-codeword latency measurement")
+    ap.add_argument("--no-bler-curve", dest="bler_curve", action="store_false",
+                    help="skip the BLER sweep over Eb/N0 of the headline workload")
     return ap.parse_args()
 
 
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(x: float) -> float:
+    """The largest value of x over the ranks of the process group (x itself without one);
+    the tensor lives where the backend needs it (CUDA for NCCL, host for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbps(world: int, steps: int, batch: int, K: int, seconds: float) -> float:
+    """Whole-job information throughput: every rank decodes `batch` codewords per step."""
+    return world * steps * batch * K / seconds / 1e9
 
 
 def make_inputs(batch: int, rank: int, ebn0: float = EBN0):
@@ -257,6 +277,31 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
             "traffic": "BG1|BG2 x Z{32..384} x R{1/3..8/9} x QPSK/16QAM/64QAM int8"
                        + (f"; {learned_share:.3f} of blocks learned (BG2 Z=128 R=1/5 "
                           "binary16, 10 iterations)" if learned is not None else "")}
+
+
+# ----------------------------------------------------------- BLER over the Eb/N0 sweep
+
+def bler_curve_measure(graph, batch: int = 1024, ebn0s=None):
+    """The headline workload's Eb/N0 sweep (0.5 .. 2.5 dB in 0.25 dB steps, batch 1024,
+    int8 offset min-sum, cap 10 iterations with the stopping rule): BLER and mean
+    iterations per point, decoded on the GPU."""
+    import numpy as np
+    import torch
+
+    import paper_2009_05534_gb300 as ldpc
+    if ebn0s is None:
+        ebn0s = [0.5 + 0.25 * k for k in range(9)]
+    pts = []
+    for eb in ebn0s:
+        wl = make_inputs(batch, 0, eb)
+        bits, iters = ldpc.decode(graph, torch.from_numpy(wl.llr_int8()).cuda(), T_ITER,
+                                  early_stop=True)
+        got = ldpc.unpack_bits(bits.cpu().numpy(), wl.K)
+        pts.append({"ebn0_db": eb, "bler": float((got != wl.info).any(1).mean()),
+                    "ber": float((got != wl.info).mean()),
+                    "mean_iterations": float(iters.float().mean())})
+    return {"workload": "BG1-shaped Z=384 R=1/3 QPSK int8 offset-1, cap 10, stopping rule, "
+                        f"{batch} codewords per point", "points": pts}
 
 
 # ------------------------------------------------------------------- single-codeword latency
@@ -563,14 +608,8 @@ def run_ours(args):
     clocks = sampler.stop()
     graph.sync_status(stream)
     per = [a.elapsed_time(b) / 1e3 for a, b in ev]         # seconds per step (= per launch)
-    elapsed = ev[0][0].elapsed_time(ev[-1][1]) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    bits_total = world * args.steps * B * wl.K
-    value = bits_total / elapsed / 1e9
+    elapsed = max_over_ranks(ev[0][0].elapsed_time(ev[-1][1]) / 1e3)
+    value = job_gbps(world, args.steps, B, wl.K, elapsed)
     kern = sum(per) / len(per)
 
     # early stop on (same data, 10-iteration cap): mean iterations and throughput
@@ -596,13 +635,8 @@ def run_ours(args):
     for _ in range(args.steps):
         ldpc.decode_host(graph, pin, T_ITER, bits=hbits, iters=hit, stream=stream,
                          early_stop=False)
-    e2e_t = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e = world * args.steps * B * wl.K / e2e_t / 1e9
+    e2e_t = max_over_ranks(time.perf_counter() - t0)
+    e2e = job_gbps(world, args.steps, B, wl.K, e2e_t)
 
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(local)
@@ -617,6 +651,7 @@ def run_ours(args):
 
     serving = serving_measure(args.serve_slots) if args.serve_slots > 0 else None
     latency = latency_measure(wl, graph) if args.latency else None
+    bler_curve = bler_curve_measure(graph) if args.bler_curve else None
     flooding = flooding_measure(wl, graph, bufs[0]) if args.flooding else None
     high_load = high_load_measure() if args.high_load else None
     learned = learned_measure() if args.learned else None
@@ -653,6 +688,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": B * (nbytes + 4)},
             "serving": serving,
             "latency": latency,
+            "bler_curve": bler_curve,
             "flooding": flooding,
             "high_load": high_load,
             "learned": learned,

@@ -95,3 +95,33 @@ def test_list_rejects_unsupported(ldpc):
     with pytest.raises(ldpc.LdpcError):
         ldpc.decode_list([(g, llr, bits, it, 0, 0, 5)])
     g.close()
+
+
+@pytest.mark.parametrize("dtype", ["int8", "fp16", "fp32"])
+def test_decode_rows_equals_gathered_batch(ldpc, dtype):
+    """Row-mapped decode: codeword b reads pool row in_rows[b] and writes output row
+    out_rows[b]; equal to decoding the gathered rows as a plain batch."""
+    wl = make_workload("BG1", 128, 40, 2.0, seed=17, graph_seed=0)
+    host = {"int8": wl.llr_int8(), "fp16": wl.llr_fp16(), "fp32": wl.llr}[dtype]
+    kw = {} if dtype == "int8" else dict(algo=ldpc.NORMALISED, alpha=0.75)
+    g = ldpc.Graph(wl.base, wl.K_b, 128)
+    pool = torch.from_numpy(host).cuda()
+    rng = np.random.default_rng(5)
+    in_rows = rng.choice(40, 25, replace=False).astype(np.int32)
+    out_rows = rng.permutation(64)[:25].astype(np.int32)
+    nb = (wl.K + 7) // 8
+    bits = torch.zeros((64, nb), dtype=torch.uint8, device="cuda")
+    iters = torch.zeros((64,), dtype=torch.int32, device="cuda")
+    ldpc.decode_rows(g, pool, torch.from_numpy(in_rows).cuda(), torch.from_numpy(out_rows).cuda(),
+                     6, bits=bits, iters=iters, **kw)
+    ref_b, ref_i = ldpc.decode(g, pool[torch.from_numpy(in_rows).long().cuda()], 6, **kw)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits.cpu().numpy()[out_rows], ref_b.cpu().numpy())
+    assert np.array_equal(iters.cpu().numpy()[out_rows], ref_i.cpu().numpy())
+    untouched = np.setdiff1d(np.arange(64), out_rows)
+    assert (bits.cpu().numpy()[untouched] == 0).all()
+    with pytest.raises(ValueError):
+        ldpc.decode_rows(g, pool, torch.tensor([40], dtype=torch.int32, device="cuda"),
+                         torch.tensor([0], dtype=torch.int32, device="cuda"), 6, bits=bits,
+                         iters=iters, **kw)
+    g.close()
