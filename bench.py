@@ -291,17 +291,21 @@ def bler_curve_measure(graph, batch: int = 1024, ebn0s=None):
     import paper_2009_05534_gb300 as ldpc
     if ebn0s is None:
         ebn0s = [0.5 + 0.25 * k for k in range(9)]
-    pts = []
-    for eb in ebn0s:
-        wl = make_inputs(batch, 0, eb)
-        bits, iters = ldpc.decode(graph, torch.from_numpy(wl.llr_int8()).cuda(), T_ITER,
-                                  early_stop=True)
-        got = ldpc.unpack_bits(bits.cpu().numpy(), wl.K)
-        pts.append({"ebn0_db": eb, "bler": float((got != wl.info).any(1).mean()),
-                    "ber": float((got != wl.info).mean()),
-                    "mean_iterations": float(iters.float().mean())})
-    return {"workload": "BG1-shaped Z=384 R=1/3 QPSK int8 offset-1, cap 10, stopping rule, "
-                        f"{batch} codewords per point", "points": pts}
+    out = {"workload": "BG1-shaped Z=384 R=1/3 QPSK int8 offset-1, cap 10, stopping rule, "
+                       f"{batch} codewords per point; LLR scale 4 (the headline quantiser) "
+                       "and scale 2 (same kernel, coarser input quantisation)"}
+    for scale in (4.0, 2.0):
+        pts = []
+        for eb in ebn0s:
+            wl = make_inputs(batch, 0, eb)
+            bits, iters = ldpc.decode(graph, torch.from_numpy(wl.llr_int8(scale)).cuda(),
+                                      T_ITER, early_stop=True)
+            got = ldpc.unpack_bits(bits.cpu().numpy(), wl.K)
+            pts.append({"ebn0_db": eb, "bler": float((got != wl.info).any(1).mean()),
+                        "ber": float((got != wl.info).mean()),
+                        "mean_iterations": float(iters.float().mean())})
+        out[f"scale_{scale:g}"] = pts
+    return out
 
 
 # ------------------------------------------------------------------- single-codeword latency
