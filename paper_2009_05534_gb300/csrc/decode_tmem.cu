@@ -14,8 +14,13 @@
 //
 // Mapping (per codeword half of the block): thread w owns check rows w and w + H
 // (H = Z/2) of every layer, carried as two binary16 lanes (exact for 8-bit values); the
-// posterior words, bias-by-1152 representation, circulant gather with half swap, and
-// xorsign min-sum are those described in decode_rowpair.cu.  Messages are stored as
+// posterior words, circulant gather with half swap, and xorsign min-sum follow
+// decode_rowpair.cu, with two changes that move work from the integer / min-max pipe to the
+// FMA pipe: posteriors are biased by 1279 (binary16 L + 1279 on [1152, 1406]) so that
+// v + 127 = (L + 1279) - (c + 1152) is one subtraction, and the saturation of v to
+// [-127, 127] is done by two relu FMAs, y = max(v + 127, 0), z = max(254 - y, 0),
+// sat(v) = 127 - z (exact on these integers); the second minimum comes from plain
+// min / max of magnitudes.  Messages are stored as
 // bytes c + 128, two edges per 32-bit TMEM column, packed tightly across rows (edge e at
 // column e/2, byte pair e%2), so a row's messages arrive with one or two tcgen05.ld per
 // thread and leave with one or two tcgen05.st; a column shared with the neighbouring row
@@ -29,6 +34,12 @@ namespace {
 
 using namespace h2;
 using namespace tm;
+
+// posterior representation: binary16 L + 1279 (exact, spacing 1 on [1152, 1406])
+constexpr uint32_t kPostBias = 0x64FF64FFu;   // 1279 = L of 0
+constexpr uint32_t kPostLo = 0x64806480u;     // 1152 = -127 + 1279
+constexpr uint32_t kPostHi = 0x657E657Eu;     // 1406 =  127 + 1279
+constexpr uint32_t k254 = 0x5BF05BF0u;        // 254.0
 
 struct EdgeMetaT {
     int base_nw;       // c*H + u
@@ -82,10 +93,13 @@ __device__ __forceinline__ void tm_row(const EdgeMetaT *meta, uint32_t *Lb, uint
         // message byte pair -> binary16 (c + 1152) under the exponent byte 0x64
         const uint32_t M =
             prmt(cm[(P + j) >> 1], 0x64646464u, ((P + j) & 1) ? 0x4342u : 0x4140u);
-        uint32_t x = h2sub(X[j], M);
-        x = h2max(h2min(x, kP127), kN127);
-        const uint32_t hi = h2maxxs(m1, x);
-        m2 = h2minxs(m2, hi);
+        // v = sat(L - c) from posteriors biased by 1279 through two relu FMAs (exact for
+        // these integers): y = max(L - c + 127, 0), z = max(254 - y, 0), v = 127 - z
+        const uint32_t y = h2relu_fma(M, kNegOne2, X[j]);
+        const uint32_t z = h2relu_fma(y, kNegOne2, k254);
+        const uint32_t x = h2sub(kP127, z);
+        // m2 from plain min / max of magnitudes; m1 carries the sign product
+        m2 = h2min(m2, h2max(h2abs(m1), h2abs(x)));
         m1 = h2minxs(m1, x);
         X[j] = x;
     }
@@ -100,8 +114,8 @@ __device__ __forceinline__ void tm_row(const EdgeMetaT *meta, uint32_t *Lb, uint
         const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
         const uint32_t sg = (x & kSign2) ^ SO;                 // S xor sgn(x), as +-1.0
         C[j] = h2fma(ex, sg, kBias2);                          // c' + 1152
-        uint32_t L = h2add(C[j], x);                           // (x + c') + 1152
-        L = h2max(h2min(L, kLbHi), kLbLo);
+        uint32_t L = h2add(C[j], h2add(x, kP127));             // (x + c') + 1279
+        L = h2max(h2min(L, kPostHi), kPostLo);
         if (store) Lb[addr[j]] = prmt(L, 0u, sel[j]);
     }
     // repack: low bytes of both lanes of each edge; foreign halves of the boundary columns
@@ -153,7 +167,7 @@ __device__ __forceinline__ uint32_t tm_parity(const EdgeMetaT *meta, const uint3
         const EdgeMetaT mt = meta[e0 + j];
         const bool wr = w >= mt.thresh;
         const int a = w + mt.base_nw - (wr ? H : 0);
-        par ^= h2lt_mask(prmt(Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kBias2);
+        par ^= h2lt_mask(prmt(Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kPostBias);
     }
     return par;
 }
@@ -236,11 +250,10 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                 for (int c = 0; c < n_cols; ++c) {
                     for (int j = ht; j < H; j += nthr_half) {
                         const int t0 = c * Z + j - lo, t1 = t0 + H;
-                        const uint32_t b0 =
-                            (t0 >= 0 && t0 < p.n_tx) ? ((uint32_t)(uint8_t)src[t0] ^ 0x80u) : 0x80u;
-                        const uint32_t b1 =
-                            (t1 >= 0 && t1 < p.n_tx) ? ((uint32_t)(uint8_t)src[t1] ^ 0x80u) : 0x80u;
-                        Lb[c * H + j] = 0x64006400u | b0 | (b1 << 16);
+                        // binary16 L + 1279 = 1024 + (L + 255): bit pattern 0x6400 + L + 255
+                        const int q0 = (t0 >= 0 && t0 < p.n_tx) ? (int)src[t0] : 0;
+                        const int q1 = (t1 >= 0 && t1 < p.n_tx) ? (int)src[t1] : 0;
+                        Lb[c * H + j] = (uint32_t)(0x64FF + q0) | ((uint32_t)(0x64FF + q1) << 16);
                     }
                 }
                 named_sync(bar_id, nthr_half);
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                         const int lane = i >= H ? 1 : 0;
                         const uint32_t wd = Lb[c * H + i - lane * H];
                         const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-                        if (h < 0x6480u) x |= 1u << kk;
+                        if (h < 0x64FFu) x |= 1u << kk;
                     }
                     p.bits[out_row(p, cw) * nbytes + b] = (uint8_t)x;
                 }
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
                             const int lane = i >= H ? 1 : 0;
                             const uint32_t wd = Lb[c * H + i - lane * H];
                             const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-                            po[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
+                            po[c * Z + i] = (int8_t)((int)h - 0x64FF);
                         }
                 }
                 if (p.c2v) {

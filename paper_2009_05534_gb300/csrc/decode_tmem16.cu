@@ -119,8 +119,7 @@ __device__ __forceinline__ void row16(const EdgeMeta16 *meta, uint32_t *Lb, uint
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const uint32_t x = h2sub(X[j], cm[j]);          // a2: v = L - c_old
-        const uint32_t hi = h2maxxs(m1, x);
-        m2 = h2minxs(m2, hi);
+        m2 = h2min(m2, h2max(h2abs(m1), h2abs(x)));     // second minimum of |v|
         m1 = h2minxs(m1, x);                            // carries the sign product
         X[j] = x;
     }
