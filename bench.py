@@ -653,12 +653,14 @@ def run_ours(args):
     alg_bytes = B * (wl.n_tx + nbytes + 4)
     traffic = profiled_traffic("layered_int8_bg1_z384")
 
-    serving = serving_measure(args.serve_slots) if args.serve_slots > 0 else None
-    latency = latency_measure(wl, graph) if args.latency else None
-    bler_curve = bler_curve_measure(graph) if args.bler_curve else None
-    flooding = flooding_measure(wl, graph, bufs[0]) if args.flooding else None
-    high_load = high_load_measure() if args.high_load else None
-    learned = learned_measure() if args.learned else None
+    # the single-GPU side measurements run on rank 0 only (replicas would repeat them)
+    aux = rank == 0
+    serving = serving_measure(args.serve_slots) if aux and args.serve_slots > 0 else None
+    latency = latency_measure(wl, graph) if aux and args.latency else None
+    bler_curve = bler_curve_measure(graph) if aux and args.bler_curve else None
+    flooding = flooding_measure(wl, graph, bufs[0]) if aux and args.flooding else None
+    high_load = high_load_measure() if aux and args.high_load else None
+    learned = learned_measure() if aux and args.learned else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -709,6 +711,7 @@ def run_ours(args):
     graph.close()
     if world > 1:
         import torch.distributed as dist
+        dist.barrier()
         dist.destroy_process_group()
     return 0
 
