@@ -10,12 +10,13 @@
 //   register as two binary16 lanes.  The 8-bit LLRs are integers in [-127, 127]; every
 //   intermediate value is an integer of magnitude below 2048, so binary16 holds it
 //   exactly and the results are bit-identical to 8-bit fixed-point arithmetic.
-// * Posteriors in shared memory are stored biased by 1152: a word holds
-//   (L[cZ+j] + 1152, L[cZ+j+H] + 1152) for j < H.  Biased values lie in [1025, 1279],
-//   where binary16 has spacing 1, and the bit pattern of 1024 + b is 0x6400 | b.
+// * Posteriors in shared memory are stored biased by 1279: a word holds
+//   (L[cZ+j] + 1279, L[cZ+j+H] + 1279) for j < H.  Biased values lie in [1152, 1406],
+//   where binary16 has spacing 1, and the bit pattern of 1024 + b is 0x6400 + b.
 // * Check-to-variable messages are kept expanded, one byte per (edge, row), as c + 128.
 //   One PRMT that inserts the byte under the exponent 0x64 turns it into binary16
-//   c + 1152, so v = (L + 1152) - (c + 1152) needs no further conversion, and the new
+//   c + 1152, so (L + 1279) - (c + 1152) = v + 127 is one subtraction; two relu FMAs
+//   give sat(v) = 127 - max(254 - max(v + 127, 0), 0) without min/max, and the new
 //   message c' + 1152 = fma(|m'|, +-1, 1152) is stored back by taking its low byte.
 // * Circulant gather: row j (< H) of a circulant with shift s = qH + u reads word
 //   (j + u) mod H with its halves exchanged when q xor [j + u >= H]; the same
@@ -94,10 +95,10 @@ __device__ __forceinline__ void process_row(const Smem &s, int e0, int H, int w,
         const uint32_t sl = wr ? mt.sel_w : mt.sel_nw;
         const uint32_t X = prmt(s.Lb[a], 0u, sl);
         const uint32_t M = prmt((uint32_t)s.c2v[(e0 + j) * H + w], 0x64646464u, 0x4140u);
-        uint32_t x = h2sub(X, M);
-        x = h2max(h2min(x, kP127), kN127);
-        const uint32_t hi = h2maxxs(m1, x);
-        m2 = h2minxs(m2, hi);
+        // sat(L - c) through two relu FMAs: y = max(v + 127, 0), z = max(254 - y, 0)
+        const uint32_t y = h2relu_fma(M, kNegOne2, X);
+        const uint32_t x = h2sub(kP127, h2relu_fma(y, kNegOne2, k254));
+        m2 = h2min(m2, h2max(h2abs(m1), h2abs(x)));
         m1 = h2minxs(m1, x);
         v[j] = x;
         addr[j] = a;
@@ -113,8 +114,8 @@ __device__ __forceinline__ void process_row(const Smem &s, int e0, int H, int w,
         const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
         const uint32_t sg = (x & kSign2) ^ SO;                 // S xor sgn(x), as +-1.0
         const uint32_t Cm = h2fma(ex, sg, kBias2);             // c' + 1152
-        uint32_t Lb = h2add(Cm, x);                            // (x + c') + 1152
-        Lb = h2max(h2min(Lb, kLbHi), kLbLo);
+        uint32_t Lb = h2add(Cm, h2add(x, kP127));              // (x + c') + 1279
+        Lb = h2max(h2min(Lb, kPostHi), kPostLo);
         if (store) {
             s.Lb[addr[j]] = prmt(Lb, 0u, sel[j]);
             s.c2v[(e0 + j) * H + w] = (uint16_t)prmt(Cm, 0u, 0x3320u);
@@ -140,14 +141,14 @@ __device__ __forceinline__ void dispatch_row(int d, const Smem &s, int e0, int H
     }
 }
 
-// parity of the hard decisions (L < 0  <=>  biased value < 1152) of row pair w
+// parity of the hard decisions (L < 0  <=>  biased value < 1279) of row pair w
 __device__ __forceinline__ uint32_t row_parity(const Smem &s, int e0, int d, int H, int w) {
     uint32_t par = 0;
     for (int j = 0; j < d; ++j) {
         const EdgeMeta mt = s.meta[e0 + j];
         const bool wr = w >= mt.thresh;
         const int a = w + mt.base_nw - (wr ? H : 0);
-        par ^= h2lt_mask(prmt(s.Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kBias2);
+        par ^= h2lt_mask(prmt(s.Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kPostBias);
     }
     return par;
 }
@@ -165,11 +166,10 @@ __device__ void decode_codeword(const CwArgs &a, const Smem &s) {
     for (int c = 0; c < n_cols; ++c)
         for (int j = tid; j < H; j += nthr) {
             const int t0 = c * Z + j - lo, t1 = t0 + H;
-            const uint32_t b0 =
-                (t0 >= 0 && t0 < a.n_tx) ? ((uint32_t)(uint8_t)a.llr[t0] ^ 0x80u) : 0x80u;
-            const uint32_t b1 =
-                (t1 >= 0 && t1 < a.n_tx) ? ((uint32_t)(uint8_t)a.llr[t1] ^ 0x80u) : 0x80u;
-            s.Lb[c * H + j] = 0x64006400u | b0 | (b1 << 16);
+            // binary16 L + 1279 = 1024 + (L + 255): bit pattern 0x6400 + L + 255
+            const int q0 = (t0 >= 0 && t0 < a.n_tx) ? (int)a.llr[t0] : 0;
+            const int q1 = (t1 >= 0 && t1 < a.n_tx) ? (int)a.llr[t1] : 0;
+            s.Lb[c * H + j] = (uint32_t)(0x64FF + q0) | ((uint32_t)(0x64FF + q1) << 16);
         }
     {
         uint32_t *c2 = reinterpret_cast<uint32_t *>(s.c2v);
@@ -212,7 +212,7 @@ __device__ void decode_codeword(const CwArgs &a, const Smem &s) {
             const int lane = i >= H ? 1 : 0;
             const uint32_t wd = s.Lb[c * H + i - lane * H];
             const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-            if (h < 0x6480u) x |= 1u << kk;
+            if (h < 0x64FFu) x |= 1u << kk;
         }
         a.bits[b] = (uint8_t)x;
     }
@@ -223,7 +223,7 @@ __device__ void decode_codeword(const CwArgs &a, const Smem &s) {
                 const int lane = i >= H ? 1 : 0;
                 const uint32_t wd = s.Lb[c * H + i - lane * H];
                 const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
-                a.post[c * Z + i] = (int8_t)(uint8_t)((h & 0xffu) ^ 0x80u);
+                a.post[c * Z + i] = (int8_t)((int)h - 0x64FF);
             }
     if (a.c2v)
         for (int e = 0; e < E; ++e)

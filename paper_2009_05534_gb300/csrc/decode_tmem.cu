@@ -35,12 +35,6 @@ namespace {
 using namespace h2;
 using namespace tm;
 
-// posterior representation: binary16 L + 1279 (exact, spacing 1 on [1152, 1406])
-constexpr uint32_t kPostBias = 0x64FF64FFu;   // 1279 = L of 0
-constexpr uint32_t kPostLo = 0x64806480u;     // 1152 = -127 + 1279
-constexpr uint32_t kPostHi = 0x657E657Eu;     // 1406 =  127 + 1279
-constexpr uint32_t k254 = 0x5BF05BF0u;        // 254.0
-
 struct EdgeMetaT {
     int base_nw;       // c*H + u
     int thresh;        // H - u

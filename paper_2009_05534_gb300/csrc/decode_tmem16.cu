@@ -178,23 +178,23 @@ __device__ __forceinline__ uint32_t parity16(const EdgeMeta16 *meta, const uint3
     return par & kSign2;
 }
 
-// kCw = 2: two codewords per block, every message in TMEM.  kCw = 1: one codeword per
-// block for shapes whose messages do not fit twice; the first tm_warps warps keep their
-// messages in TMEM and the remaining threads in shared memory.
-template <int kCw>
+// kCw codewords per block (1, 2 or 4).  Without kHybrid every message is in TMEM; with it
+// the first tm_warps warps keep their messages in TMEM and the remaining threads in shared
+// memory (shapes whose messages do not fit TMEM for every warp of the block).
+template <int kCw, bool kHybrid>
 __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ Tmem16Params pp) {
     const DecodeParams &p = pp.p;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tmem_base;
-    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ __align__(8) uint64_t s_bar[kCw];
     const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nthr_half = pp.wpc * 32;
-    const int half = kCw == 2 ? tid / nthr_half : 0;  // codeword slot of this thread
+    const int half = kCw > 1 ? tid / nthr_half : 0;   // codeword slot of this thread
     const int ht = tid - half * nthr_half;            // thread index within the codeword
     const bool store = ht < H;
     const int w = store ? ht : H - 1;                 // spare threads shadow the last row pair
-    const bool use_tm = kCw == 2 || warp < pp.tm_warps;
+    const bool use_tm = !kHybrid || warp < pp.tm_warps;
     EdgeMeta16 *s_meta = reinterpret_cast<EdgeMeta16 *>(smem);
     uint32_t *Lb = reinterpret_cast<uint32_t *>(smem + pp.off_lb) + (size_t)half * n_cols * H;
     const uint16_t *stage =
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
                             beta2 = h2_from_float(q[0]);
                             ngamma2 = h2_from_float(-q[1]);
                         }
-                        if (kCw == 2 || use_tm)
+                        if (use_tm)
                             dispatch16<true>(d, s_meta, Lb, tbase + (uint32_t)e0, sm, ns, e0, H,
                                              w, store, beta2, ngamma2);
                         else
@@ -349,25 +349,20 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
     if (warp == 0) tmem_dealloc(s_tmem_base, (uint32_t)pp.tcols);
 }
 
-// Block shape: kCw = 2 when two codewords' messages fit in TMEM, else kCw = 1 with the
-// warps beyond the TMEM capacity keeping their messages in shared memory.
+// Block shape: codewords per block, warps per codeword, warps with messages in TMEM (the
+// rest in shared memory), and TMEM columns allocated.
 struct Shape16 {
     int cw, wpc, tm_warps, ns, tcols;
 };
 
-Shape16 shape16(const DecodeParams &p) {
+Shape16 make_shape16(const DecodeParams &p, int cw) {
     Shape16 s;
-    const int H = p.Z / 2;
-    s.wpc = (H + 31) / 32;
+    s.cw = cw;
+    s.wpc = (p.Z / 2 + 31) / 32;
     const int fit = p.E > 0 ? kTmemCols16 / p.E : 0;       // column regions that fit
-    if ((2 * s.wpc + 3) / 4 <= fit) {
-        s.cw = 2;
-        s.tm_warps = 2 * s.wpc;
-    } else {
-        s.cw = 1;
-        s.tm_warps = s.wpc < 4 * fit ? s.wpc : 4 * fit;
-    }
-    s.ns = s.cw == 1 ? (s.wpc - s.tm_warps) * 32 : 0;
+    const int warps = cw * s.wpc;
+    s.tm_warps = warps < 4 * fit ? warps : 4 * fit;
+    s.ns = (warps - s.tm_warps) * 32;
     const int need = ((s.tm_warps + 3) / 4) * p.E;
     s.tcols = 32;
     while (s.tcols < need) s.tcols <<= 1;
@@ -395,6 +390,21 @@ Layout16 layout16(const DecodeParams &p, const Shape16 &sh, bool tma) {
     return l;
 }
 
+// Preference: four codewords per block when its warps fit one block (small Z), the shared
+// memory holds them and the batch fills every SM with more than two codewords (throughput);
+// else two codewords with every message in TMEM (also the lower-latency choice for small
+// batches, which then spread over more SMs); else one.
+Shape16 shape16(const DecodeParams &p, size_t smem_optin, int n_sm) {
+    const int wpc = (p.Z / 2 + 31) / 32;
+    if (4 * wpc <= 12 && p.batch > 2 * n_sm) {
+        const Shape16 s4 = make_shape16(p, 4);
+        if (s4.tm_warps >= 1 && layout16(p, s4, false).total <= smem_optin) return s4;
+    }
+    const Shape16 s2 = make_shape16(p, 2);
+    if (s2.ns == 0) return s2;
+    return make_shape16(p, 1);
+}
+
 }  // namespace
 
 bool tmem16_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin) {
@@ -402,7 +412,9 @@ bool tmem16_supported(const DecodeParams &p, int llr_type, int max_deg, size_t s
     if (p.algo != LDPC_NORMALISED && p.algo != LDPC_OFFSET && p.algo != LDPC_LEARNED) return false;
     if ((p.Z & 1) || p.Z < 2 || p.Z > 384 || max_deg > kMaxDeg16 || max_deg < 2) return false;
     if (p.E > kMaxEdges16 || p.n_rows > kMaxRows16) return false;
-    const Shape16 sh = shape16(p);
+    // supported when the two-codeword or one-codeword shape fits (the four-codeword shape
+    // is an alternative for large batches only)
+    const Shape16 sh = shape16(p, smem_optin, 1 << 30);
     if (sh.tm_warps < 1 || sh.tcols > kTmemCols16) return false;
     return layout16(p, sh, false).total <= smem_optin;
 }
@@ -411,7 +423,11 @@ ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream) {
     static thread_local Tmem16Params pp;   // ~9 kB: kept off the stack
     pp.p = p;
     const int H = p.Z / 2;
-    const Shape16 sh = shape16(p);
+    int dev = 0, smem_optin = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const Shape16 sh = shape16(p, (size_t)smem_optin, n_sm);
     pp.H = H;
     pp.wpc = sh.wpc;
     pp.tcols = sh.tcols;
@@ -435,10 +451,6 @@ ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream) {
         pp.meta[e].sel_nw = q ? 0x1032u : 0x3210u;
         pp.meta[e].sel_w = q ? 0x3210u : 0x1032u;
     }
-    int dev = 0, smem_optin = 0, n_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const bool aligned = ((uintptr_t)p.llr % 16 == 0) && (p.n_tx % 8 == 0) && p.n_tx > 0;
     pp.use_tma = (aligned && layout16(p, sh, true).total <= (size_t)smem_optin) ? 1 : 0;
     const Layout16 l = layout16(p, sh, pp.use_tma != 0);
@@ -446,7 +458,10 @@ ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream) {
     pp.off_msg = (int)l.off_msg;
     pp.off_stage = (int)l.off_stage;
     pp.stage_bytes = (int)l.stage_bytes;
-    auto kern = sh.cw == 2 ? tmem16_kernel<2> : tmem16_kernel<1>;
+    const bool hybrid = sh.ns > 0;
+    auto kern = sh.cw == 4 ? (hybrid ? tmem16_kernel<4, true> : tmem16_kernel<4, false>)
+              : sh.cw == 2 ? tmem16_kernel<2, false>
+                           : (hybrid ? tmem16_kernel<1, true> : tmem16_kernel<1, false>);
     // blocks per SM: as many as shared memory and the 512 TMEM columns allow; the shared
     // memory request is raised so that no more blocks fit than TMEM can hold (a block
     // beyond that would only wait in tcgen05.alloc)

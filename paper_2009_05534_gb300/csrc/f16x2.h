@@ -17,6 +17,12 @@ constexpr uint32_t kInf2 = 0x7C007C00u;
 constexpr uint32_t kSign2 = 0x80008000u;
 constexpr uint32_t kAbs2 = 0x7FFF7FFFu;
 constexpr int kMaxDeg = 20;
+// 8-bit decoders: posteriors held as binary16 L + 1279 (exact, spacing 1 on [1152, 1406]),
+// so that v + 127 = (L + 1279) - (c + 1152) is one subtraction
+constexpr uint32_t kPostBias = 0x64FF64FFu;   // 1279: L = 0
+constexpr uint32_t kPostLo = 0x64806480u;     // 1152: L = -127
+constexpr uint32_t kPostHi = 0x657E657Eu;     // 1406: L = 127
+constexpr uint32_t k254 = 0x5BF05BF0u;        // 254.0
 
 
 

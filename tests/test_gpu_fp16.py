@@ -155,3 +155,37 @@ def test_large_batch_sampled(ldpc):
                                 alpha=0.75, max_iter=10, early_stop=True, threads=8)
     assert np.array_equal(gb[idx], ref.bits)
     assert np.array_equal(it[idx], ref.iters)
+
+
+@pytest.mark.parametrize("kind,Z,mode", [("BG2", 128, "learned"), ("BG1", 64, "normalised75"),
+                                         ("BG2", 94, "offset")])
+def test_four_codeword_blocks_large_batch(ldpc, kind, Z, mode):
+    """Batches larger than two codewords per SM at small Z run four codewords per block
+    (BG2 Z=128: four warps' messages in TMEM, four in shared memory; BG1 Z=64: all in TMEM);
+    sampled codewords match the oracle in every posterior and message."""
+    B, T = 400, 6
+    wl = make_workload(kind, Z, B, 2.0, seed=300 + Z, graph_seed=0)
+    h = wl.llr_fp16()
+    if mode == "learned":
+        tab = _table(T, wl.n_rows, 12)
+        kw_o, kw_g = (dict(algo=oracle.LEARNED, learned=tab),
+                      dict(algo=ldpc.LEARNED, learned=torch.from_numpy(tab).cuda()))
+    elif mode == "offset":
+        kw_o, kw_g = dict(algo=oracle.OFFSET, offset=0.3), dict(algo=ldpc.OFFSET, offset=0.3)
+    else:
+        kw_o = dict(algo=oracle.NORMALISED, alpha=0.75)
+        kw_g = dict(algo=ldpc.NORMALISED, alpha=0.75)
+    g = ldpc.Graph(wl.base, wl.K_b, Z)
+    bits, iters, post, c2v = ldpc.decode(g, torch.from_numpy(h).cuda(), T, early_stop=True,
+                                         debug=True, **kw_g)
+    torch.cuda.synchronize()
+    g.sync_status()
+    idx = np.sort(np.random.default_rng(Z).choice(B, 24, replace=False))
+    ref = oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, h[idx], max_iter=T,
+                                early_stop=True, want_post=True, want_c2v=True, threads=8,
+                                **kw_o)
+    assert np.array_equal(ldpc.unpack_bits(bits.cpu().numpy()[idx], wl.K), ref.bits)
+    assert np.array_equal(iters.cpu().numpy()[idx], ref.iters)
+    assert np.array_equal(post.cpu().numpy()[idx], ref.post)
+    assert np.array_equal(c2v.cpu().numpy()[idx], ref.c2v)
+    g.close()
