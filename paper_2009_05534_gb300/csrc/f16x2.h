@@ -9,10 +9,7 @@ namespace h2 {
 constexpr uint32_t kOne2 = 0x3C003C00u;     // (1.0, 1.0)
 constexpr uint32_t kNegOne2 = 0xBC00BC00u;  // (-1.0, -1.0)
 constexpr uint32_t kP127 = 0x57F057F0u;     // 127.0
-constexpr uint32_t kN127 = 0xD7F0D7F0u;     // -127.0
-constexpr uint32_t kBias2 = 0x64806480u;    // 1152.0
-constexpr uint32_t kLbLo = 0x64016401u;     // 1025.0 = -127 + 1152
-constexpr uint32_t kLbHi = 0x64FF64FFu;     // 1279.0 =  127 + 1152
+constexpr uint32_t kBias2 = 0x64806480u;    // 1152.0: message byte c + 128 under exponent 0x64
 constexpr uint32_t kInf2 = 0x7C007C00u;
 constexpr uint32_t kSign2 = 0x80008000u;
 constexpr uint32_t kAbs2 = 0x7FFF7FFFu;
