@@ -140,6 +140,9 @@ ldpc_status ldpc_graph_destroy(ldpc_graph_t h) {
     cudaFree(g->d_row_ptr);
     cudaFree(g->d_status);
     cudaFree(g->d_stage);
+    for (int k = 0; k < Graph::kHostChunks; ++k)
+        if (g->chunk_ev[k]) cudaEventDestroy(g->chunk_ev[k]);
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     delete g;
     return LDPC_OK;
 }
@@ -315,24 +318,57 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
         }
         g->stage_bytes = need;
     }
+    if (!g->copy_stream) {
+        if (cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return LDPC_ERR_CUDA;
+        for (int k = 0; k < Graph::kHostChunks; ++k)
+            if (cudaEventCreateWithFlags(&g->chunk_ev[k], cudaEventDisableTiming) != cudaSuccess)
+                return LDPC_ERR_CUDA;
+    }
     char *base = (char *)g->d_stage;
-    void *d_llr = base;
+    char *d_llr = base;
     uint8_t *d_bits = (uint8_t *)(base + up(in_b));
     int32_t *d_it = (int32_t *)(base + up(in_b) + up(bits_b));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(d_llr, llr_host, in_b, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return LDPC_ERR_CUDA;
-    ldpc_status st = decode_common(h, d_llr, batch, max_iter, stream, &o, d_bits, d_it,
-                                   nullptr, nullptr);
-    if (st != LDPC_OK) {
-        cudaStreamSynchronize(s);
-        return st;
+    // Pipeline: the inputs go up in chunks of one wave of codewords (two per SM) on the
+    // graph's copy stream, and the decode of chunk k waits only for chunk k's upload, so
+    // later uploads overlap earlier decodes; each chunk's outputs come back on `stream`
+    // right after its decode.  A wave-sized chunk needs the same number of passes of the
+    // batch kernels as the whole batch would.
+    int dev = 0, n_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    int chunk = 2 * n_sm;
+    if ((batch + chunk - 1) / chunk > Graph::kHostChunks)
+        chunk = (batch + Graph::kHostChunks - 1) / Graph::kHostChunks;
+    const int n_chunks = (batch + chunk - 1) / chunk;
+    for (int k = 0; k < n_chunks; ++k) {
+        const size_t b0 = (size_t)k * chunk;
+        const size_t nb = (size_t)(batch - (int)b0 < chunk ? batch - (int)b0 : chunk);
+        if (cudaMemcpyAsync(d_llr + b0 * n_tx * esz, (const char *)llr_host + b0 * n_tx * esz,
+                            nb * n_tx * esz, cudaMemcpyHostToDevice,
+                            g->copy_stream) != cudaSuccess ||
+            cudaEventRecord(g->chunk_ev[k], g->copy_stream) != cudaSuccess)
+            return LDPC_ERR_CUDA;
     }
-    if (cudaMemcpyAsync(hard_bits_host, d_bits, bits_b, cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(iters_host, d_it, it_b, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return LDPC_ERR_CUDA;
+    for (int k = 0; k < n_chunks; ++k) {
+        const size_t b0 = (size_t)k * chunk;
+        const int nb = batch - (int)b0 < chunk ? batch - (int)b0 : chunk;
+        if (cudaStreamWaitEvent(s, g->chunk_ev[k], 0) != cudaSuccess) return LDPC_ERR_CUDA;
+        ldpc_status st = decode_common(h, d_llr + b0 * n_tx * esz, nb, max_iter, stream, &o,
+                                       d_bits + b0 * nbytes, d_it + b0, nullptr, nullptr);
+        if (st != LDPC_OK) {
+            cudaStreamSynchronize(g->copy_stream);
+            cudaStreamSynchronize(s);
+            return st;
+        }
+        if (cudaMemcpyAsync(hard_bits_host + b0 * nbytes, d_bits + b0 * nbytes, nb * nbytes,
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(iters_host + b0, d_it + b0, nb * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return LDPC_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LDPC_ERR_CUDA;
     return LDPC_OK;
 }
 

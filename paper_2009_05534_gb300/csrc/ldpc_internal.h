@@ -28,10 +28,14 @@ struct Graph {
     int *d_row_ptr = nullptr;            // device [M_bg + 1]
     int *d_status = nullptr;             // device status word (ldpc_status of the first error)
     int device = 0;
-    // staging buffers of ldpc_decode_host (guarded by host_mu)
+    // staging buffers of ldpc_decode_host (guarded by host_mu): device copies of the
+    // inputs and outputs, a copy stream, and one event per chunk of the pipelined upload
     std::mutex host_mu;
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    static constexpr int kHostChunks = 16;
+    cudaEvent_t chunk_ev[kHostChunks] = {};
 };
 
 // Everything a decode kernel needs, passed by value.

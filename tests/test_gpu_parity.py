@@ -264,3 +264,27 @@ def test_int8_dense_bg1_table_z384(ldpc):
     assert np.array_equal(post.cpu().numpy(), ref.post)
     assert np.array_equal(c2v.cpu().numpy(), ref.c2v)
     g.close()
+
+
+# ------------------------------------------------------------------ host-buffer entry point
+
+@pytest.mark.parametrize("B,pinned", [(700, True), (40, False), (1, True)])
+def test_decode_host_equals_device_decode(ldpc, B, pinned):
+    """ldpc_decode_host uploads in wave-sized chunks that overlap the decodes (700 = two full
+    chunks and a ragged one); results equal the device-buffer decode, from pinned or pageable
+    host memory."""
+    wl = make_workload("BG1", 128, B, 1.75, seed=B)
+    q = wl.llr_int8()
+    g = ldpc.Graph(wl.base, wl.K_b, 128)
+    host = torch.from_numpy(q)
+    if pinned:
+        host = host.pin_memory()
+    hb, hi = ldpc.decode_host(g, host, 8, early_stop=True)
+    db, di = ldpc.decode(g, torch.from_numpy(q).cuda(), 8, early_stop=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(hb.numpy(), db.cpu().numpy())
+    assert np.array_equal(hi.numpy(), di.cpu().numpy())
+    ref = oracle.decode_layered(wl.base, wl.K_b, 128, wl.n_rows, q[:8], algo=oracle.OFFSET,
+                                max_iter=8, early_stop=True, threads=8)
+    assert np.array_equal(ldpc.unpack_bits(hb.numpy()[:8], wl.K), ref.bits)
+    g.close()
