@@ -276,6 +276,17 @@ ldpc_status ldpc_decode_flooding(ldpc_graph_t g, const float *llr_dev, int batch
                                  uint8_t *hard_bits_dev, int32_t *iters_dev, float *post_dev,
                                  float *workspace_dev);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): launches a kernel
+ * that waits on a shared-memory barrier armed for a transfer that is never issued, with at
+ * most spin_limit polls (1 .. the decoders' own limit, 4 194 304), and returns the status
+ * that wait produced: LDPC_ERR_TIMEOUT when it gave up as designed (the decoders then
+ * record the same code in the graph's status word and return), LDPC_ERR_INVALID_ARG for a
+ * bad limit, LDPC_ERR_CUDA on a launch error.  Nothing stays in flight; the context remains
+ * usable.  cycles_out (host, may be NULL) receives the SM cycles the wait took.
+ * Synchronous on `stream`. */
+ldpc_status ldpc_selftest_wait_timeout(unsigned int spin_limit, ldpc_stream_t stream,
+                                       unsigned long long *cycles_out);
+
 /* Wait for the graph's outstanding work on `stream` and return (then clear) the device
  * status word: LDPC_OK, or the first error a kernel reported (e.g. LDPC_ERR_TIMEOUT). */
 ldpc_status ldpc_graph_sync_status(ldpc_graph_t g, ldpc_stream_t stream);

@@ -54,7 +54,8 @@ ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_dest
                "ldpc_decode_host", "ldpc_decode_list", "ldpc_decode_list_noalloc",
                "ldpc_learned_workspace_floats", "ldpc_learned_forward", "ldpc_learned_backward",
                "ldpc_learned_forward_iter", "ldpc_learned_backward_iter",
-               "ldpc_flooding_workspace_floats", "ldpc_decode_flooding", "ldpc_decode_rows")
+               "ldpc_flooding_workspace_floats", "ldpc_decode_flooding", "ldpc_decode_rows",
+               "ldpc_selftest_wait_timeout")
 
 
 def lib():
@@ -99,6 +100,9 @@ def lib():
             L.ldpc_decode_rows.argtypes = [P, P, P, P, i, i, P, ctypes.POINTER(DecodeOpts),
                                            P, P]
             L.ldpc_decode_rows.restype = i
+            L.ldpc_selftest_wait_timeout.argtypes = [ctypes.c_uint, P,
+                                                     ctypes.POINTER(ctypes.c_ulonglong)]
+            L.ldpc_selftest_wait_timeout.restype = i
             L.ldpc_flooding_workspace_floats.argtypes = [P, i, i]
             L.ldpc_flooding_workspace_floats.restype = ctypes.c_size_t
             L.ldpc_decode_flooding.argtypes = [P, P, i, i, P, ctypes.POINTER(DecodeOpts), P, P,
@@ -234,6 +238,13 @@ def decode(graph: Graph, llr, max_iter: int, *, bits=None, iters=None, stream=No
                                    ctypes.c_void_p(post.data_ptr()),
                                    ctypes.c_void_p(c2v.data_ptr())), "ldpc_decode_debug")
     return bits, iters, post, c2v
+
+
+def selftest_wait_timeout(spin_limit: int = 1 << 16, stream=None):
+    """Run the bounded-wait self-test; returns (status code, SM cycles the wait took)."""
+    cyc = ctypes.c_ulonglong(0)
+    st = lib().ldpc_selftest_wait_timeout(int(spin_limit), _stream_ptr(stream), ctypes.byref(cyc))
+    return st, int(cyc.value)
 
 
 def decode_rows(graph: Graph, llr, in_rows, out_rows, max_iter: int, *, bits, iters,

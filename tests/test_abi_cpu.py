@@ -82,3 +82,9 @@ def test_flooding_and_learned_entry_points_reject_null_graph(L):
     assert L.ldpc_learned_forward_iter(None, None, 1, 10, 0, 0, None, None, None, None) == 1
     assert L.ldpc_learned_backward_iter(None, None, 1, 10, 0, 0, None, None, None, None, None,
                                         0) == 1
+
+
+def test_selftest_rejects_bad_limits_on_host(L):
+    L.ldpc_selftest_wait_timeout.argtypes = [ctypes.c_uint, ctypes.c_void_p, ctypes.c_void_p]
+    assert L.ldpc_selftest_wait_timeout(0, None, None) == 1
+    assert L.ldpc_selftest_wait_timeout((1 << 22) + 1, None, None) == 1

@@ -288,3 +288,19 @@ def test_decode_host_equals_device_decode(ldpc, B, pinned):
                                 max_iter=8, early_stop=True, threads=8)
     assert np.array_equal(ldpc.unpack_bits(hb.numpy()[:8], wl.K), ref.bits)
     g.close()
+
+
+# ------------------------------------------------------- bounded waits (failure handling)
+
+def test_bounded_wait_times_out_and_context_survives(ldpc):
+    """A barrier armed for a transfer that never comes: the bounded wait gives up and reports
+    LDPC_ERR_TIMEOUT (no trap, no hang), and the next decode on the same context is exact."""
+    st, cycles = ldpc.selftest_wait_timeout(1 << 14)
+    assert st == 5                                   # LDPC_ERR_TIMEOUT
+    assert cycles > 0
+    wl = make_workload("BG1", 64, 4, 2.0, seed=5)
+    q = wl.llr_int8()
+    bits, iters = _gpu(ldpc, wl, q, 3, early_stop=False, debug=False)
+    ref = oracle.decode_layered(wl.base, wl.K_b, 64, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=3, early_stop=False)
+    assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
