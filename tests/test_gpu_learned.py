@@ -205,3 +205,42 @@ def test_trained_table_gains_over_plain_min_sum(ldpc):
     bler_l = (ldpc.unpack_bits(bits_l.cpu().numpy(), wl.K) != wl.info).any(1).mean()
     assert bler_p > 0.5 and bler_l < 0.02, (bler_p, bler_l)
     g.close()
+
+
+def test_checkpoint_resume_equals_uninterrupted(ldpc, tmp_path):
+    """Training 3 steps, stopping, and resuming from the checkpoint to 6 steps gives the same
+    table as 6 uninterrupted steps (deterministic kernels, Adam state restored)."""
+    from paper_2009_05534_gb300 import learned
+    wl = make_workload("BG2", 16, 256, 1.5, modulation="BPSK", seed=44)
+    g = ldpc.Graph(wl.base, wl.K_b, 16)
+    llr = torch.from_numpy(wl.llr).cuda()
+    cw = torch.from_numpy(wl.codewords).cuda()
+
+    def batch(k):
+        sl = slice((k % 4) * 64, (k % 4) * 64 + 64)
+        return llr[sl], cw[sl]
+
+    w = np.full(4, 0.25)
+    ref, _ = learned.train(g, wl.n_rows, 4, batch, n_steps=6, lr=1e-2, iter_weights=w,
+                           detach=True)
+    ck = tmp_path / "ck.pt"
+    learned.train(g, wl.n_rows, 4, batch, n_steps=3, lr=1e-2, iter_weights=w, detach=True,
+                  checkpoint=ck)
+    res, hist = learned.train(g, wl.n_rows, 4, batch, n_steps=6, lr=1e-2, iter_weights=w,
+                              detach=True, checkpoint=ck)
+    assert len(hist) == 6
+    assert torch.equal(res, ref)
+    g.close()
+
+
+def test_training_recipe_end_to_end(ldpc, tmp_path):
+    """The training command on a tiny budget: generates, trains, evaluates, writes a table
+    that loads back with its recipe."""
+    from paper_2009_05534_gb300 import train_learned
+    out = tmp_path / "t.json"
+    train_learned.main(["--Z", "16", "--T", "4", "--codewords", "2048", "--batch", "512",
+                        "--epochs", "1", "--lr", "0.01", "--eval-codewords", "512",
+                        "--eval-grid", "2.0:3.0:0.5", "--out", str(out)])
+    table, meta = train_learned.load_table(out)
+    assert table.shape == (4, 42, 2) and np.isfinite(table).all()
+    assert meta["training"]["steps"] == 4 and len(meta["eval"]["bler_plain"]) == 3
