@@ -11,7 +11,9 @@ rate arrive continuously; at every slot boundary the server
    (admission by memory: a block that does not fit waits for a later slot),
 3. decodes everything admitted in that slot with one work-list launch (`ldpc_decode_list`)
    on the next stream of a small round-robin pool, so new slots start while earlier ones
-   are still running on the device.
+   are still running on the device; blocks for the learned decoder (one graph and
+   (beta, gamma) table, binary16 LLRs) go to one row-mapped launch (`ldpc_decode_rows`) on
+   a stream of their own, and the slot completes when both have.
 
 Graphs live on the device for the server's lifetime.  Channel LLRs are read from device
 memory (the demapper's output buffers); the decoder's messages and posteriors never leave
