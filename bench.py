@@ -312,18 +312,21 @@ def bler_curve_measure(graph, batch: int = 1024, ebn0s=None):
 
 def latency_measure(wl, graph, reps: int = 50):
     """Latency of one codeword alone (batch 1, the headline workload, 10 iterations, early
-    stop off): CUDA events around each launch on an otherwise idle stream; median and max."""
+    stop off): CUDA events around each launch on an otherwise idle stream; median and max.
+    int8 with the paper's two strategies (Sec. IV): alpha = 1 thread per row pair (the
+    high-throughput kernel) and alpha = 2, 4 cooperating threads per row pair (the
+    low-latency kernel, the library's choice for a batch that does not fill the SMs), and
+    the binary16 decoder.  Then small batches (up to two codewords per SM) with alpha 1, 2
+    and 4, which sets where the library switches strategy."""
     import torch
 
     import paper_2009_05534_gb300 as ldpc
     stream = torch.cuda.Stream()
     q = torch.from_numpy(wl.llr_int8()[:1]).cuda()
-    out = {}
-    for name, dt in (("int8", q), ("fp16", torch.from_numpy(wl.llr_fp16()[:1]).cuda())):
-        kw = dict(algo=ldpc.OFFSET) if name == "int8" else dict(algo=ldpc.NORMALISED,
-                                                                alpha=0.75)
+
+    def lat(dt, n, **kw):
         ts = []
-        for k in range(reps + 3):
+        for k in range(n + 3):
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.record(stream)
             ldpc.decode(graph, dt, T_ITER, early_stop=False, stream=stream, **kw)
@@ -331,8 +334,24 @@ def latency_measure(wl, graph, reps: int = 50):
             torch.cuda.synchronize()
             if k >= 3:
                 ts.append(s.elapsed_time(e) * 1e3)
-        out[name] = {"median_us": statistics.median(ts), "max_us": max(ts),
-                     "per_iteration_us": statistics.median(ts) / T_ITER}
+        return {"median_us": statistics.median(ts), "max_us": max(ts),
+                "per_iteration_us": statistics.median(ts) / T_ITER}
+
+    out = {"int8": lat(q, reps, algo=ldpc.OFFSET)}
+    out["int8_by_alpha"] = {str(a): lat(q, reps, algo=ldpc.OFFSET, threads_per_row=a)
+                            for a in (1, 2, 4)}
+    out["fp16"] = lat(torch.from_numpy(wl.llr_fp16()[:1]).cuda(), reps, algo=ldpc.NORMALISED,
+                      alpha=0.75)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    small = {}
+    full = wl.llr_int8()
+    for b in sorted({1, n_sm // 4, n_sm // 2, n_sm, 2 * n_sm}):
+        if b > full.shape[0]:
+            continue
+        qb = torch.from_numpy(full[:b]).cuda()
+        small[str(b)] = {str(a): lat(qb, 10, algo=ldpc.OFFSET, threads_per_row=a)["median_us"]
+                         for a in (1, 2, 4)}
+    out["batch_us_by_alpha"] = small
     return {"workload": "one BG1-shaped Z=384 R=1/3 codeword, 10 iterations", **out}
 
 
@@ -448,12 +467,20 @@ def flooding_measure(wl, graph, q_dev, batch: int = 512, reps: int = 3):
 # -------------------------------------------------------- learned vs plain (BG2, Z = 128)
 
 LEARNED_TABLE = "learned_bg2_z128_t10.json"
+# (table file, base graph, Z, Eb/N0 grid of the comparison, fresh codewords per point,
+# throughput batch) of each trained table: the grids bracket both decoders' BLER 1e-2
+LEARNED_CASES = (
+    (LEARNED_TABLE, "BG2", 128,
+     (1.5, 1.75, 2.0, 2.25, 2.5, 2.75, 3.0, 3.5, 3.75, 4.0, 4.25), 8192, 8192),
+    ("learned_bg1_z384_t10.json", "BG1", 384,
+     (0.75, 0.875, 1.0, 1.125, 1.25, 1.375, 1.5), 4096, 2048),
+)
 
 
-def learned_measure(n_cw: int = 8192,
-                    grid=(1.5, 1.75, 2.0, 2.25, 2.5, 2.75, 3.0, 3.5, 3.75, 4.0, 4.25),
-                    batch: int = 8192, reps: int = 5):
-    """The trained (beta, gamma) table against plain normalised min-sum (alpha 0.75) on the
+def learned_measure(table_file: str = LEARNED_TABLE, kind: str = "BG2", Z: int = 128,
+                    grid=LEARNED_CASES[0][3], n_cw: int = 8192, batch: int = 8192,
+                    reps: int = 5):
+    """A trained (beta, gamma) table against plain normalised min-sum (alpha 0.75) on the
     same fresh codewords: BLER per Eb/N0 at T = 10 (binary16 LLRs and messages), the Eb/N0
     of BLER 1e-2 for each, and decode throughput of both at T = 10 and, with early stop,
     at the plain decoder's BLER-1e-2 point."""
@@ -463,27 +490,27 @@ def learned_measure(n_cw: int = 8192,
     from paper_2009_05534_gb300.train_learned import (TABLE_DIR, bler_sweep, ebn0_at,
                                                       load_table)
     from synth import make_workload
-    path = os.path.join(TABLE_DIR, LEARNED_TABLE)
+    path = os.path.join(TABLE_DIR, table_file)
     if not os.path.exists(path):
         return None
     table, meta = load_table(path)
     T = int(meta["T"])
-    wl0 = make_workload("BG2", 128, 1, 1.0, seed=0, graph_seed=0)
-    g = ldpc.Graph(wl0.base, wl0.K_b, 128)
+    wl0 = make_workload(kind, Z, 1, 1.0, seed=0, graph_seed=0)
+    g = ldpc.Graph(wl0.base, wl0.K_b, Z)
     tab = torch.from_numpy(table).cuda()
-    curves = bler_sweep(g, "BG2", 128, T, {"plain": None, "learned": tab}, list(grid), n_cw,
+    curves = bler_sweep(g, kind, Z, T, {"plain": None, "learned": tab}, list(grid), n_cw,
                         4096, seed=77_000)
     at = {k: ebn0_at(list(grid), v, 1e-2) for k, v in curves.items()}
     eb_op = at["plain"] if at["plain"] is not None else grid[-1]
     stream = torch.cuda.Stream()
     thr = {}
+    wl = make_workload(kind, Z, batch, float(eb_op), seed=78_000, graph_seed=0)
+    host = wl.llr_fp16()
+    n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
+    with torch.cuda.stream(stream):
+        bufs = [torch.from_numpy(host).cuda() for _ in range(n_copies)]
+    torch.cuda.synchronize()
     for es in (False, True):
-        wl = make_workload("BG2", 128, batch, float(eb_op), seed=78_000, graph_seed=0)
-        host = wl.llr_fp16()
-        n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
-        with torch.cuda.stream(stream):
-            bufs = [torch.from_numpy(host).cuda() for _ in range(n_copies)]
-        torch.cuda.synchronize()
         for name, kw in (("plain", dict(algo=ldpc.NORMALISED, alpha=0.75)),
                          ("learned", dict(algo=ldpc.LEARNED, learned=tab))):
             iters = None
@@ -498,13 +525,13 @@ def learned_measure(n_cw: int = 8192,
             sec = _timed(run, reps, stream)
             thr[f"{name}{'_early_stop' if es else ''}"] = {
                 "gbps": batch * wl.K / sec / 1e9, "mean_iterations": float(iters.float().mean())}
-        del bufs
+    del bufs
     g.close()
     return {"workload": meta.get("code"), "T": T, "llr": "binary16", "eval_codewords": n_cw,
             "ebn0_db": list(grid), "bler_plain": curves["plain"],
             "bler_learned": curves["learned"], "ebn0_at_bler_1e-2": at,
             "gain_db": (at["plain"] - at["learned"]) if None not in at.values() else None,
-            "throughput_ebn0_db": eb_op, "throughput": thr,
+            "throughput_ebn0_db": eb_op, "throughput_batch": batch, "throughput": thr,
             "training": {k: meta["training"].get(k) for k in
                          ("codewords", "epochs", "steps", "lr", "ebn0_db", "loss", "gradient")}}
 
@@ -660,7 +687,11 @@ def run_ours(args):
     bler_curve = bler_curve_measure(graph) if aux and args.bler_curve else None
     flooding = flooding_measure(wl, graph, bufs[0]) if aux and args.flooding else None
     high_load = high_load_measure() if aux and args.high_load else None
-    learned = learned_measure() if aux and args.learned else None
+    learned = learned_bg1 = None
+    if aux and args.learned:
+        learned = learned_measure()
+        learned_bg1 = learned_measure(*LEARNED_CASES[1][:3], grid=LEARNED_CASES[1][3],
+                                      n_cw=LEARNED_CASES[1][4], batch=LEARNED_CASES[1][5])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -701,6 +732,7 @@ def run_ours(args):
             "flooding": flooding,
             "high_load": high_load,
             "learned": learned,
+            "learned_bg1": learned_bg1,
             "gpu_launches": launches,
             "clocks": clocks,
             "wall_s": t_wall,

@@ -70,7 +70,14 @@ typedef enum {
  *   punct_cols   punctured leading columns (default 2, Sec. II).
  *   early_stop   1: stop a codeword when its syndrome is zero after a full iteration.
  *   cluster_size 1 (one thread block per codeword; other values are reserved).
- *   learned_params device float [max_iter][n_rows][2] = (beta, gamma) for LDPC_LEARNED. */
+ *   learned_params device float [max_iter][n_rows][2] = (beta, gamma) for LDPC_LEARNED.
+ *   threads_per_row  the paper's alpha (Sec. IV): cooperating threads per check-row pair.
+ *                1 = the high-throughput strategy (one thread per row pair, two codewords
+ *                per thread block); 2 or 4 = the low-latency strategy (alpha threads split
+ *                each row's circulants and combine min, sub-min and sign by a log2(alpha)
+ *                step warp-shuffle reduce; one codeword per thread block); int8 only.
+ *                0 = automatic: 2 when the batch is no larger than the SM count and the
+ *                graph fits, else 1.  Results are identical for every value. */
 typedef struct {
     int llr_type;
     int algo;
@@ -83,10 +90,12 @@ typedef struct {
     int early_stop;
     int cluster_size;
     const float *learned_params;
+    int threads_per_row;
 } ldpc_decode_opts;
 
 /* Defaults: int8, offset min-sum with offset_q = 1, alpha = 0.75, all rows, n_tx from the
- * rows, punct_cols = 2, early_stop = 1, cluster_size = 1, no learned table. */
+ * rows, punct_cols = 2, early_stop = 1, cluster_size = 1, no learned table,
+ * threads_per_row = 0 (automatic). */
 void ldpc_decode_opts_default(ldpc_decode_opts *opts);
 
 /* Build a device-resident graph from a host base table (Sec. II).
@@ -117,7 +126,9 @@ int ldpc_graph_vars(ldpc_graph_t g, int n_rows);
  *   opts           NULL = defaults.
  *   hard_bits_dev  device uint8 [batch][ceil(K/8)] output.
  *   iters_dev      device int32 [batch] output: iterations executed (T without early stop).
- * Host-side argument errors return at once and launch nothing.  Returns after the launch. */
+ * Host-side argument errors return at once and launch nothing: LDPC_ERR_INVALID_ARG for a
+ * threads_per_row other than 0, 1, 2, 4, LDPC_ERR_UNSUPPORTED for 2 or 4 outside the
+ * int8 offset decoder or for graphs it cannot hold.  Returns after the launch. */
 ldpc_status ldpc_decode(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
                         ldpc_stream_t stream, const ldpc_decode_opts *opts,
                         uint8_t *hard_bits_dev, int32_t *iters_dev);

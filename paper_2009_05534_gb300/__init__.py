@@ -41,7 +41,7 @@ class DecodeOpts(ctypes.Structure):
                 ("offset", ctypes.c_float), ("offset_q", ctypes.c_int), ("n_rows", ctypes.c_int),
                 ("n_tx", ctypes.c_int), ("punct_cols", ctypes.c_int),
                 ("early_stop", ctypes.c_int), ("cluster_size", ctypes.c_int),
-                ("learned_params", ctypes.c_void_p)]
+                ("learned_params", ctypes.c_void_p), ("threads_per_row", ctypes.c_int)]
 
 
 _lib = None
@@ -177,7 +177,8 @@ def _stream_ptr(stream):
 
 
 def make_opts(llr_type: int, *, algo=None, alpha=0.75, offset=0.0, offset_q=1, n_rows=0,
-              n_tx=0, punct_cols=2, early_stop=True, learned=None) -> DecodeOpts:
+              n_tx=0, punct_cols=2, early_stop=True, learned=None,
+              threads_per_row=0) -> DecodeOpts:
     o = DecodeOpts()
     lib().ldpc_decode_opts_default(ctypes.byref(o))
     o.llr_type = llr_type
@@ -190,6 +191,7 @@ def make_opts(llr_type: int, *, algo=None, alpha=0.75, offset=0.0, offset_q=1, n
     o.punct_cols = punct_cols
     o.early_stop = int(bool(early_stop))
     o.learned_params = None if learned is None else learned.data_ptr()
+    o.threads_per_row = int(threads_per_row)
     return o
 
 

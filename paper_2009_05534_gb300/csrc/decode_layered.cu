@@ -262,9 +262,21 @@ ldpc_status launch_t(const DecodeParams &p, cudaStream_t stream) {
 }  // namespace
 
 ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t stream) {
-    int dev = 0, smem_optin = 0;
+    int dev = 0, smem_optin = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    // the low-latency strategy (alpha cooperating threads per row pair, one codeword per
+    // block) when asked for, or by default when the batch does not fill the SMs
+    int A = p.threads_per_row;
+    if (A == 0)
+        A = (p.batch <= n_sm &&
+             tmem_ll_supported(p, llr_type, p.max_deg, 2, (size_t)smem_optin)) ? 2 : 1;
+    if (A > 1) {
+        if (!tmem_ll_supported(p, llr_type, p.max_deg, A, (size_t)smem_optin))
+            return LDPC_ERR_UNSUPPORTED;
+        return launch_tmem_ll(p, A, stream);
+    }
     if (tmem_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
         return launch_tmem(p, stream);
     if (!p.in_rows && !p.out_rows && rowpair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))

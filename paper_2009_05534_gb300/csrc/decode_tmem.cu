@@ -232,10 +232,11 @@ __global__ void __launch_bounds__(384, 1) tmem_kernel(const __grid_constant__ Tm
             const int8_t *src = llr_all + in_row(p, cw) * p.n_tx;
             if (pp.use_tma) {
                 const bool ok = mbar_wait(bar, parity);
-                parity ^= 1u;
                 if (named_or(bar_id, nthr_half, !ok)) {
                     if (ht == 0) atomicCAS(p.status, 0, (int)LDPC_ERR_TIMEOUT);
-                    failed = true;
+                    failed = true;           // parity stays on the copy still in flight
+                } else {
+                    parity ^= 1u;
                 }
                 src = stage;
             }

@@ -1,0 +1,405 @@
+// Layered min-sum, 8-bit offset variant, low-latency strategy: A cooperating threads per
+// check-row pair (paper Sec. IV, the low-latency decoder: N_thread = (alpha / rho) Z with
+// rho = 2 rows per thread here, and the min / sub-min / sign of a row combined across the
+// alpha threads by a parallel reduce in log2(alpha) warp-shuffle steps, Fig. 3).
+//
+// One codeword per thread block (the decode of a lone codeword, or of a batch no larger
+// than the SM count).  Thread t serves row pair w = t / A of every layer, as cooperating
+// thread k = t % A: of a layer's d circulants it takes edges k, k + A, k + 2A, ...  Every
+// thread runs ceil(d / A) edge slots; a slot past the row's last edge is a dummy whose
+// v2c is +127 (the largest magnitude, sign +), which changes neither the minimum, the
+// second minimum nor the sign product, and which writes nothing back.
+//
+// Arithmetic, storage and exactness follow the two-codeword TMEM kernel (decode_tmem.cu):
+// posteriors as binary16 L + 1279 in shared memory, gathered per row pair with the half
+// swap; messages as bytes c + 128 in Tensor Memory, two edge slots per 32-bit column of
+// the thread's own lane, packed tightly across rows (a thread's slots of row r follow
+// those of row r - 1); saturation of v by two relu FMAs; new magnitude
+// max(m1', (m1 + m2 - 1) - |v|).  The reduce across the A threads is exact: m1 and the
+// sign product combine by min.xorsign, and m2 = min(m2a, m2b, max(|m1a|, |m1b|)).
+#include "f16x2.h"
+#include "ldpc_internal.h"
+#include "tmem.h"
+
+namespace ldpc {
+namespace {
+
+using namespace h2;
+using namespace tm;
+
+struct EdgeMetaL {
+    int base_nw;       // c*H + u
+    int thresh;        // H - u
+    uint32_t sel_nw;   // 0x3210 or 0x1032
+    uint32_t sel_w;
+};
+
+constexpr int kMaxEdgesL = 1024;
+constexpr int kMaxRowsL = 64;
+constexpr int kTmemColsL = 512;
+
+struct LlParams {
+    DecodeParams p;
+    int H;
+    int ncols;                   // TMEM columns per thread: ceil(total slots / 2)
+    int use_tma;                 // channel LLRs staged by a 1-D bulk copy
+    int off_lb, off_stage;       // shared-memory offsets of the posteriors and the staging
+    int row[kMaxRowsL + 1];      // edge offsets of the rows
+    int slot[kMaxRowsL + 1];     // slot offsets of the rows in every thread's TMEM lane
+    EdgeMetaL meta[kMaxEdgesL];
+};
+
+// --------------------------------------------------------------------------- one layer
+
+// Cooperating thread k of row pair w on a layer of degree D, with DA = ceil(D / A) slots
+// whose first slot sits in the upper half of its TMEM column when P = 1.
+template <int A, int DA, int P>
+__device__ __forceinline__ void ll_row(const EdgeMetaL *meta, uint32_t *Lb, uint32_t tcolumn,
+                                       int e0, int D, int H, int w, int k, bool store) {
+    constexpr int NC = (P + DA + 1) / 2;   // columns touched by the row's slots
+    uint32_t cm[NC];
+    twait_st();                            // this thread's earlier stores to these columns
+    tload<NC>(tcolumn, cm);
+    const bool last_real = k + A * (DA - 1) < D;
+    uint32_t X[DA];
+    int addr[DA];
+    uint32_t sel[DA];
+#pragma unroll
+    for (int i = 0; i < DA; ++i) {
+        const int j = (i == DA - 1 && !last_real) ? D - 1 : k + A * i;   // dummy reads a real edge
+        const EdgeMetaL mt = meta[e0 + j];
+        const bool wr = w >= mt.thresh;
+        addr[i] = w + mt.base_nw - (wr ? H : 0);
+        sel[i] = wr ? mt.sel_w : mt.sel_nw;
+        X[i] = prmt(Lb[addr[i]], 0u, sel[i]);
+    }
+    twait_ld();
+    uint32_t m1 = kInf2, m2 = kInf2;
+#pragma unroll
+    for (int i = 0; i < DA; ++i) {
+        const uint32_t M =
+            prmt(cm[(P + i) >> 1], 0x64646464u, ((P + i) & 1) ? 0x4342u : 0x4140u);
+        const uint32_t y = h2relu_fma(M, kNegOne2, X[i]);   // max(v + 127, 0)
+        const uint32_t z = h2relu_fma(y, kNegOne2, k254);   // max(254 - y, 0)
+        uint32_t x = h2sub(kP127, z);                       // sat(v)
+        if (i == DA - 1 && !last_real) x = kP127;
+        m2 = h2min(m2, h2max(h2abs(m1), h2abs(x)));
+        m1 = h2minxs(m1, x);
+        X[i] = x;
+    }
+    // parallel reduce across the A threads of the row pair (adjacent lanes of one warp)
+#pragma unroll
+    for (int o = 1; o < A; o <<= 1) {
+        const uint32_t o1 = __shfl_xor_sync(0xffffffffu, m1, o);
+        const uint32_t o2 = __shfl_xor_sync(0xffffffffu, m2, o);
+        m2 = h2min(h2min(m2, o2), h2max(h2abs(m1), h2abs(o1)));
+        m1 = h2minxs(m1, o1);
+    }
+    const uint32_t SO = (m1 & kSign2) | kOne2;               // +-1.0: sign product per lane
+    const uint32_t a1 = m1 & kAbs2, a2 = m2 & kAbs2;
+    const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);    // max(m1 - 1, 0)
+    const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);       // m1 + m2 - 1
+    uint32_t C[DA];
+#pragma unroll
+    for (int i = 0; i < DA; ++i) {
+        const uint32_t x = X[i];
+        const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
+        const uint32_t sg = (x & kSign2) ^ SO;
+        C[i] = h2fma(ex, sg, kBias2);                          // c' + 1152
+        uint32_t L = h2add(C[i], h2add(x, kP127));             // (x + c') + 1279
+        L = h2max(h2min(L, kPostHi), kPostLo);
+        if (store && (i < DA - 1 || last_real)) Lb[addr[i]] = prmt(L, 0u, sel[i]);
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const int jl = 2 * q - P, jh = 2 * q + 1 - P;
+        const int il = jl < 0 ? 0 : jl, ih = jh >= DA ? DA - 1 : jh;
+        if (jl >= 0 && jh < DA)
+            cm[q] = prmt(C[il], C[ih], 0x6420u);
+        else if (jl >= 0)
+            cm[q] = prmt(C[il], cm[q], 0x7620u);
+        else
+            cm[q] = prmt(cm[q], C[ih], 0x6410u);
+    }
+    tstore<NC>(tcolumn, cm);
+}
+
+template <int A, int DA>
+__device__ __forceinline__ void ll_row_any(const EdgeMetaL *meta, uint32_t *Lb, uint32_t tbase,
+                                           int s0, int e0, int D, int H, int w, int k,
+                                           bool store) {
+    if (s0 & 1)
+        ll_row<A, DA, 1>(meta, Lb, tbase + (uint32_t)(s0 >> 1), e0, D, H, w, k, store);
+    else
+        ll_row<A, DA, 0>(meta, Lb, tbase + (uint32_t)(s0 >> 1), e0, D, H, w, k, store);
+}
+
+template <int A>
+__device__ __forceinline__ void ll_dispatch(int D, const EdgeMetaL *meta, uint32_t *Lb,
+                                            uint32_t tbase, int s0, int e0, int H, int w, int k,
+                                            bool store) {
+    const int DA = (D + A - 1) / A;
+    switch (DA) {
+#define LDPC_LL_CASE(N)                                                          \
+    case N:                                                                      \
+        if constexpr (N * A < kMaxDeg + A)                                       \
+            ll_row_any<A, N>(meta, Lb, tbase, s0, e0, D, H, w, k, store);         \
+        break;
+        LDPC_LL_CASE(1) LDPC_LL_CASE(2) LDPC_LL_CASE(3) LDPC_LL_CASE(4) LDPC_LL_CASE(5)
+        LDPC_LL_CASE(6) LDPC_LL_CASE(7) LDPC_LL_CASE(8) LDPC_LL_CASE(9) LDPC_LL_CASE(10)
+#undef LDPC_LL_CASE
+    default:
+        break;
+    }
+}
+
+// parity of the hard decisions of row pair w over a row's edges, combined over the A
+// threads (each takes edges k, k + A, ...); 0 when both rows of the pair are satisfied
+template <int A>
+__device__ __forceinline__ uint32_t ll_parity(const EdgeMetaL *meta, const uint32_t *Lb, int e0,
+                                              int D, int H, int w, int k) {
+    uint32_t par = 0;
+    for (int j = k; j < D; j += A) {
+        const EdgeMetaL mt = meta[e0 + j];
+        const bool wr = w >= mt.thresh;
+        const int a = w + mt.base_nw - (wr ? H : 0);
+        par ^= h2lt_mask(prmt(Lb[a], 0u, wr ? mt.sel_w : mt.sel_nw), kPostBias);
+    }
+#pragma unroll
+    for (int o = 1; o < A; o <<= 1) par ^= __shfl_xor_sync(0xffffffffu, par, o);
+    return par;
+}
+
+// ---------------------------------------------------------------------------- the kernel
+
+template <int A>
+__global__ void __launch_bounds__(A * 192, 1) tmem_ll_kernel(const __grid_constant__ LlParams pp) {
+    const DecodeParams &p = pp.p;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tmem_base;
+    __shared__ __align__(8) uint64_t s_bar;
+    const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
+    const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x;
+    const int k = tid % A;                            // cooperating thread of the row pair
+    const bool store = tid / A < H;
+    const int w = store ? tid / A : H - 1;            // spare groups shadow the last row pair
+    // shared memory: edge metadata | posterior words | LLR staging buffer
+    EdgeMetaL *s_meta = reinterpret_cast<EdgeMetaL *>(smem);
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem + pp.off_lb);
+    const int8_t *stage = reinterpret_cast<const int8_t *>(smem + pp.off_stage);
+    uint64_t *bar = &s_bar;
+
+    for (int e = tid; e < E; e += nthr) s_meta[e] = pp.meta[e];
+    if (tid == 0 && pp.use_tma) mbar_init(bar);
+    if (warp == 0) tmem_alloc(&s_tmem_base, kTmemColsL);
+    tmem_block_sync();
+    // this warp's lane quarter and column region
+    const uint32_t tbase = s_tmem_base + ((uint32_t)((warp & 3) * 32) << 16) +
+                           (uint32_t)((warp >> 2) * pp.ncols);
+
+    const int K = p.K_b * Z;
+    const int nbytes = (K + 7) >> 3;
+    const int lo = p.punct * Z;
+    const int8_t *llr_all = reinterpret_cast<const int8_t *>(p.llr);
+    uint32_t parity = 0;
+    bool failed = false;
+    if (pp.use_tma && tid == 0 && (int)blockIdx.x < p.batch)
+        bulk_load(const_cast<int8_t *>(stage), llr_all + in_row(p, blockIdx.x) * p.n_tx,
+                  (uint32_t)p.n_tx, bar);
+
+    for (int cw = blockIdx.x; cw < p.batch && !failed; cw += gridDim.x) {
+        // a0: zero messages; biased posteriors from the channel LLRs
+        {
+            uint32_t z[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) z[q] = 0x80808080u;
+            int c = 0;
+            for (; c + 8 <= pp.ncols; c += 8) tst<8>(tbase + c, z);
+            for (; c < pp.ncols; ++c) tst<1>(tbase + c, z);
+        }
+        const int8_t *src = llr_all + in_row(p, cw) * p.n_tx;
+        if (pp.use_tma) {
+            const bool ok = mbar_wait(bar, parity);
+            if (named_or(1, nthr, !ok)) {
+                if (tid == 0) atomicCAS(p.status, 0, (int)LDPC_ERR_TIMEOUT);
+                failed = true;               // parity stays on the copy still in flight
+                break;
+            }
+            parity ^= 1u;
+            src = stage;
+        }
+        // word (c, j) holds rows j and j + H of column block c, biased by 1279
+        for (int c = 0; c < n_cols; ++c) {
+            for (int j = tid; j < H; j += nthr) {
+                const int t0 = c * Z + j - lo, t1 = t0 + H;
+                const int q0 = (t0 >= 0 && t0 < p.n_tx) ? (int)src[t0] : 0;
+                const int q1 = (t1 >= 0 && t1 < p.n_tx) ? (int)src[t1] : 0;
+                Lb[c * H + j] = (uint32_t)(0x64FF + q0) | ((uint32_t)(0x64FF + q1) << 16);
+            }
+        }
+        named_sync(1, nthr);
+        // the staging buffer is free: start the copy of the next codeword of this block
+        if (pp.use_tma && tid == 0 && cw + (int)gridDim.x < p.batch)
+            bulk_load(const_cast<int8_t *>(stage),
+                      llr_all + in_row(p, cw + gridDim.x) * p.n_tx, (uint32_t)p.n_tx, bar);
+
+        int done = p.max_iter;
+#pragma unroll 1
+        for (int t = 1; t <= p.max_iter; ++t) {
+#pragma unroll 1
+            for (int r = 0; r < n_rows; ++r) {
+                const int e0 = pp.row[r];
+                ll_dispatch<A>(pp.row[r + 1] - e0, s_meta, Lb, tbase, pp.slot[r], e0, H, w, k,
+                               store);
+                named_sync(1, nthr);
+            }
+            if (p.early_stop) {
+                int bad = 0;
+                for (int r = 0; r < n_rows && !bad; ++r) {
+                    const int e0 = pp.row[r];
+                    bad = __any_sync(0xffffffffu, ll_parity<A>(s_meta, Lb, e0,
+                                                                pp.row[r + 1] - e0, H, w, k) != 0u);
+                }
+                if (named_or(1, nthr, bad) == 0) {
+                    done = t;
+                    break;
+                }
+            }
+        }
+
+        // a6: outputs
+        for (int b = tid; b < nbytes; b += nthr) {
+            unsigned x = 0;
+            for (int kk = 0; kk < 8; ++kk) {
+                const int j = 8 * b + kk;
+                if (j >= K) break;
+                const int c = j / Z, i = j - c * Z;
+                const int lane = i >= H ? 1 : 0;
+                const uint32_t wd = Lb[c * H + i - lane * H];
+                const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                if (h < 0x64FFu) x |= 1u << kk;
+            }
+            p.bits[out_row(p, cw) * nbytes + b] = (uint8_t)x;
+        }
+        if (tid == 0) p.iters[out_row(p, cw)] = done;
+        if (p.post) {
+            int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw * n_cols * Z;
+            for (int c = 0; c < n_cols; ++c)
+                for (int i = tid; i < Z; i += nthr) {
+                    const int lane = i >= H ? 1 : 0;
+                    const uint32_t wd = Lb[c * H + i - lane * H];
+                    const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                    po[c * Z + i] = (int8_t)((int)h - 0x64FF);
+                }
+        }
+        if (p.c2v) {
+            // each thread reads its own TMEM lane: slot i of row r is edge k + A i
+            twait_st();
+            int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw * E * Z;
+            for (int r = 0; r < n_rows; ++r) {
+                const int e0 = pp.row[r], D = pp.row[r + 1] - e0;
+                const int DA = (D + A - 1) / A;
+                for (int i = 0; i < DA; ++i) {
+                    const int s = pp.slot[r] + i, j = k + A * i;
+                    uint32_t v;
+                    tld<1>(tbase + (uint32_t)(s >> 1), &v);
+                    twait_ld();
+                    const uint32_t pr = (s & 1) ? (v >> 16) : (v & 0xffffu);
+                    if (store && j < D) {
+                        co[(size_t)(e0 + j) * Z + w] = (int8_t)(uint8_t)((pr & 0xffu) ^ 0x80u);
+                        co[(size_t)(e0 + j) * Z + w + H] =
+                            (int8_t)(uint8_t)(((pr >> 8) & 0xffu) ^ 0x80u);
+                    }
+                }
+            }
+        }
+        named_sync(1, nthr);
+    }
+    // a copy that never completed must not outlive the block: wait for it (bounded)
+    if (failed && tid == 0) mbar_wait(bar, parity);
+
+    tmem_block_sync();
+    if (warp == 0) tmem_dealloc(s_tmem_base, kTmemColsL);
+}
+
+int ll_slots(const int *row_ptr, int n_rows, int A, int *slot) {
+    int s = 0;
+    for (int r = 0; r < n_rows; ++r) {
+        if (slot) slot[r] = s;
+        s += (row_ptr[r + 1] - row_ptr[r] + A - 1) / A;
+    }
+    if (slot) slot[n_rows] = s;
+    return s;
+}
+
+size_t ll_smem_bytes(const DecodeParams &p, bool tma) {
+    const int H = p.Z / 2;
+    size_t off = ((size_t)p.E * sizeof(EdgeMetaL) + 15) & ~(size_t)15;
+    off = (off + (size_t)p.n_cols * H * 4 + 15) & ~(size_t)15;
+    return off + (tma ? (size_t)p.n_tx : 0);
+}
+
+}  // namespace
+
+bool tmem_ll_supported(const DecodeParams &p, int llr_type, int max_deg, int A,
+                       size_t smem_optin) {
+    if (A != 2 && A != 4) return false;
+    if (llr_type != LDPC_LLR_INT8 || p.algo != LDPC_OFFSET || p.offset_q != 1) return false;
+    if ((p.Z & 1) || p.Z < 2 || p.Z > 384 || max_deg > kMaxDeg || max_deg < 2) return false;
+    if (p.E > kMaxEdgesL || p.n_rows > kMaxRowsL) return false;
+    const int H = p.Z / 2;
+    const int nwarps = (A * H + 31) / 32;
+    const int depth = (nwarps + 3) / 4;                  // warps sharing a lane quarter
+    const int ncols = (ll_slots(p.h_row_ptr, p.n_rows, A, nullptr) + 1) / 2;
+    if (depth * ncols > kTmemColsL) return false;
+    return ll_smem_bytes(p, true) + 64 <= smem_optin;
+}
+
+ldpc_status launch_tmem_ll(const DecodeParams &p, int A, cudaStream_t stream) {
+    static thread_local LlParams pp;     // ~17 kB: kept off the stack
+    pp.p = p;
+    const int H = p.Z / 2;
+    pp.H = H;
+    for (int r = 0; r <= p.n_rows; ++r) pp.row[r] = p.h_row_ptr[r];
+    pp.ncols = (ll_slots(p.h_row_ptr, p.n_rows, A, pp.slot) + 1) / 2;
+    for (int e = 0; e < p.E; ++e) {
+        const uint32_t ed = p.h_edges[e];
+        const int c = (int)(ed >> 16), sh = (int)(ed & 0xffffu);
+        const int q = sh >= H ? 1 : 0, u = sh - q * H;
+        pp.meta[e].base_nw = c * H + u;
+        pp.meta[e].thresh = H - u;
+        pp.meta[e].sel_nw = q ? 0x1032u : 0x3210u;
+        pp.meta[e].sel_w = q ? 0x3210u : 0x1032u;
+    }
+    // bulk copies need 16-byte aligned rows; at least 120 kB of shared memory so that one
+    // block occupies the SM (its TMEM allocation takes all 512 columns)
+    pp.use_tma = ((reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0 && (p.n_tx % 16) == 0 &&
+                  p.n_tx > 0 && p.n_tx < (1 << 20))
+                     ? 1
+                     : 0;
+    pp.off_lb = (int)(((size_t)p.E * sizeof(EdgeMetaL) + 15) & ~(size_t)15);
+    pp.off_stage = (pp.off_lb + p.n_cols * H * 4 + 15) & ~15;
+    size_t smem = ll_smem_bytes(p, pp.use_tma != 0);
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int threads = ((A * H + 31) / 32) * 32;
+    int grid = p.batch < n_sm ? p.batch : n_sm;
+    cudaError_t err;
+    if (A == 2) {
+        err = cudaFuncSetAttribute(tmem_ll_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+        if (err == cudaSuccess) tmem_ll_kernel<2><<<grid, threads, smem, stream>>>(pp);
+    } else {
+        err = cudaFuncSetAttribute(tmem_ll_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+        if (err == cudaSuccess) tmem_ll_kernel<4><<<grid, threads, smem, stream>>>(pp);
+    }
+    if (err != cudaSuccess) return LDPC_ERR_CUDA;
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+}  // namespace ldpc

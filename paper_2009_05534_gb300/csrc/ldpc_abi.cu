@@ -48,6 +48,7 @@ void ldpc_decode_opts_default(ldpc_decode_opts *o) {
     o->punct_cols = 2;
     o->early_stop = 1;
     o->cluster_size = 1;
+    o->threads_per_row = 0;
     o->learned_params = nullptr;
 }
 
@@ -188,6 +189,11 @@ static ldpc_status decode_params(ldpc_graph_t h, const void *llr, int batch, int
     if (o.llr_type == LDPC_LLR_INT8 && o.algo != LDPC_OFFSET) return LDPC_ERR_UNSUPPORTED;
     if (o.algo == LDPC_LEARNED && !o.learned_params) return LDPC_ERR_INVALID_ARG;
     if (o.cluster_size != 1) return LDPC_ERR_UNSUPPORTED;
+    if (o.threads_per_row != 0 && o.threads_per_row != 1 && o.threads_per_row != 2 &&
+        o.threads_per_row != 4)
+        return LDPC_ERR_INVALID_ARG;
+    if (o.threads_per_row > 1 && (o.llr_type != LDPC_LLR_INT8 || flooding))
+        return LDPC_ERR_UNSUPPORTED;
     const int n_rows = o.n_rows == 0 ? g->M_bg : o.n_rows;
     if (n_rows < 1 || n_rows > g->M_bg) return LDPC_ERR_INVALID_ARG;
     const int n_cols = g->K_b + n_rows;
@@ -235,6 +241,7 @@ static ldpc_status decode_params(ldpc_graph_t h, const void *llr, int batch, int
     p.status = g->d_status;
     p.in_rows = nullptr;
     p.out_rows = nullptr;
+    p.threads_per_row = o.threads_per_row;
     *o_out = o;
     return LDPC_OK;
 }

@@ -59,6 +59,7 @@ struct DecodeParams {
     int *status;              // device status word
     const int32_t *in_rows;   // [batch] LLR row of codeword b, or null (row b)
     const int32_t *out_rows;  // [batch] output row of codeword b, or null (row b)
+    int threads_per_row;      // cooperating threads per row pair (0 = automatic)
 };
 
 // source and destination rows of codeword b of a batch (identity without row maps)
@@ -87,6 +88,12 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
 // Two-codeword row-pair kernel with messages in Tensor Memory (decode_tmem.cu).
 bool tmem_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream);
+
+// One-codeword kernel with A = 2 or 4 cooperating threads per row pair, messages in
+// Tensor Memory (decode_tmem_ll.cu): the low-latency strategy.
+bool tmem_ll_supported(const DecodeParams &p, int llr_type, int max_deg, int A,
+                       size_t smem_optin);
+ldpc_status launch_tmem_ll(const DecodeParams &p, int A, cudaStream_t stream);
 
 // Row-pair fp16x2 kernel for 8-bit offset min-sum, messages in shared memory
 // (decode_rowpair.cu).

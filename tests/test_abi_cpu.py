@@ -48,6 +48,9 @@ def test_default_opts(L):
     assert (o.llr_type, o.algo, o.offset_q, o.punct_cols, o.early_stop, o.cluster_size) == \
         (pkg.LLR_INT8, pkg.OFFSET, 1, 2, 1, 1)
     assert abs(o.alpha - 0.75) < 1e-7
+    assert o.threads_per_row == 0
+    # the binding's structure has the header's size (the last field is threads_per_row)
+    assert ctypes.sizeof(pkg.DecodeOpts) == 56
 
 
 def test_invalid_args_rejected_on_host(L):

@@ -50,29 +50,46 @@ def _unpack(ldpc, packed, K):
 
 
 # ------------------------------------------------------------------- int8 (headline path)
+#
+# threads_per_row (the paper's alpha): 1 = the high-throughput kernels (one thread per row
+# pair), 2 and 4 = the low-latency kernel (alpha threads per row pair, shuffle reduce),
+# 0 = the library's choice for the batch.
 
+_REF = {}
+
+
+def _ref_bg1(T):
+    """Oracle decode of the 24-codeword BG1 Z=384 case (shared by every alpha)."""
+    if T not in _REF:
+        wl = make_workload("BG1", 384, 24, 1.25, seed=11)
+        q = wl.llr_int8()
+        _REF[T] = (wl, q, oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q,
+                                                algo=oracle.OFFSET, offset_q=1, max_iter=T,
+                                                early_stop=False, want_post=True,
+                                                want_c2v=True, threads=8))
+    return _REF[T]
+
+
+@pytest.mark.parametrize("tpr", [1, 2, 4])
 @pytest.mark.parametrize("T", [1, 2, 5, 10])
-def test_int8_bg1_z384_bit_exact(ldpc, T):
-    wl = make_workload("BG1", 384, 24, 1.25, seed=11)
-    q = wl.llr_int8()
-    ref = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q, algo=oracle.OFFSET,
-                                offset_q=1, max_iter=T, early_stop=False, want_post=True,
-                                want_c2v=True, threads=8)
-    bits, iters, post, c2v = _gpu(ldpc, wl, q, T, early_stop=False)
+def test_int8_bg1_z384_bit_exact(ldpc, T, tpr):
+    wl, q, ref = _ref_bg1(T)
+    bits, iters, post, c2v = _gpu(ldpc, wl, q, T, early_stop=False, threads_per_row=tpr)
     assert np.array_equal(post, ref.post)
     assert np.array_equal(c2v, ref.c2v)
     assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
     assert (iters == T).all()
 
 
+@pytest.mark.parametrize("tpr", [1, 4])
 @pytest.mark.parametrize("ebn0", [0.5, 1.5, 2.5])
-def test_int8_early_stop_iterations_exact(ldpc, ebn0):
+def test_int8_early_stop_iterations_exact(ldpc, ebn0, tpr):
     wl = make_workload("BG1", 384, 32, ebn0, seed=3)
     q = wl.llr_int8()
     ref = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q, algo=oracle.OFFSET,
                                 offset_q=1, max_iter=10, early_stop=True, want_post=True,
                                 threads=8)
-    bits, iters, post, _ = _gpu(ldpc, wl, q, 10, early_stop=True)
+    bits, iters, post, _ = _gpu(ldpc, wl, q, 10, early_stop=True, threads_per_row=tpr)
     assert np.array_equal(iters, ref.iters)
     assert np.array_equal(post, ref.post)
     assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
@@ -81,15 +98,17 @@ def test_int8_early_stop_iterations_exact(ldpc, ebn0):
 @pytest.mark.parametrize("kind,Z,rate", [("BG1", 13, None), ("BG1", 40, "1/2"),
                                          ("BG2", 7, "2/3"), ("BG2", 96, "1/3"),
                                          ("BG1", 384, "8/9"), ("BG2", 2, None)])
-def test_int8_ragged_shapes_and_rates(ldpc, kind, Z, rate):
-    """Z not a multiple of the warp, odd Z, several row counts (rates)."""
+@pytest.mark.parametrize("tpr", [1, 0])
+def test_int8_ragged_shapes_and_rates(ldpc, kind, Z, rate, tpr):
+    """Z not a multiple of the warp, odd Z, several row counts (rates); with the library's
+    choice of alpha (the low-latency kernel for even Z at this batch)."""
     wl = make_workload(kind, Z, 9, 2.0, rate=None if rate is None else Fraction(rate), seed=4)
     q = wl.llr_int8()
     ref = oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, q, algo=oracle.OFFSET,
                                 offset_q=1, max_iter=6, early_stop=True, want_post=True,
                                 want_c2v=True)
     bits, iters, post, c2v = _gpu(ldpc, wl, q, 6, early_stop=True, n_rows=wl.n_rows,
-                                  n_tx=wl.n_tx)
+                                  n_tx=wl.n_tx, threads_per_row=tpr)
     assert np.array_equal(iters, ref.iters)
     assert np.array_equal(post, ref.post)
     assert np.array_equal(c2v, ref.c2v)
@@ -147,6 +166,10 @@ def test_invalid_calls_raise(ldpc):
         ldpc.decode(g, q, 5, algo=ldpc.NORMALISED)   # int8 supports offset only
     with pytest.raises(ldpc.LdpcError):
         ldpc.decode(g, q, 5, n_tx=10 ** 6)
+    with pytest.raises(ldpc.LdpcError):
+        ldpc.decode(g, q, 5, threads_per_row=3)      # alpha must be 0, 1, 2 or 4
+    with pytest.raises(ldpc.LdpcError):                # low latency: int8 offset only
+        ldpc.decode(g, q.float(), 5, threads_per_row=2)
     g.close()
 
 
@@ -213,8 +236,10 @@ def test_int8_full_batch_sampled(ldpc):
     assert (iters == 10).all()
 
 
-def test_int8_custom_table_degrees_11_to_18(ldpc):
-    """A user base table with row degrees 11..18 (the predicated wide-row path)."""
+@pytest.mark.parametrize("tpr", [1, 2, 4])
+def test_int8_custom_table_degrees_11_to_18(ldpc, tpr):
+    """A user base table with row degrees 11..18 (the predicated wide-row path; with alpha
+    2 and 4, rows whose degree is not a multiple of alpha)."""
     rng = np.random.default_rng(7)
     M, K_b, Z = 6, 24, 32
     N = K_b + M
@@ -231,7 +256,7 @@ def test_int8_custom_table_degrees_11_to_18(ldpc):
                                 max_iter=4, early_stop=False, want_post=True, want_c2v=True)
     g = ldpc.Graph(base, K_b, Z)
     bits, iters, post, c2v = ldpc.decode(g, torch.from_numpy(llr).cuda(), 4, early_stop=False,
-                                         debug=True)
+                                         debug=True, threads_per_row=tpr)
     torch.cuda.synchronize()
     assert np.array_equal(post.cpu().numpy(), ref.post)
     assert np.array_equal(c2v.cpu().numpy(), ref.c2v)
@@ -239,9 +264,11 @@ def test_int8_custom_table_degrees_11_to_18(ldpc):
     g.close()
 
 
-def test_int8_dense_bg1_table_z384(ldpc):
-    """A 46 x 68 table with more edges than fit the Tensor-Memory message store (E > 340
-    at Z = 384), which takes the shared-memory row-pair kernel."""
+@pytest.mark.parametrize("tpr", [1, 4])
+def test_int8_dense_bg1_table_z384(ldpc, tpr):
+    """A 46 x 68 table with more edges than fit the two-codeword Tensor-Memory message
+    store (E > 340 at Z = 384): alpha 1 takes the shared-memory row-pair kernel; the
+    one-codeword low-latency kernel holds it in Tensor Memory."""
     rng = np.random.default_rng(11)
     M, K_b, Z = 46, 22, 384
     N = K_b + M
@@ -259,11 +286,67 @@ def test_int8_dense_bg1_table_z384(ldpc):
                                 threads=6)
     g = ldpc.Graph(base, K_b, Z)
     bits, iters, post, c2v = ldpc.decode(g, torch.from_numpy(llr).cuda(), 3, early_stop=False,
-                                         debug=True)
+                                         debug=True, threads_per_row=tpr)
     torch.cuda.synchronize()
     assert np.array_equal(post.cpu().numpy(), ref.post)
     assert np.array_equal(c2v.cpu().numpy(), ref.c2v)
     g.close()
+
+
+# ------------------------------------------------- low-latency strategy (alpha threads)
+
+def test_low_latency_batch_beyond_sm_count(ldpc):
+    """alpha = 2 asked for on a batch larger than the SM count: each block loops over several
+    codewords, staging the next one's LLRs while it decodes; sampled codewords and every
+    iteration count match the oracle."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    B = 2 * n_sm + 7
+    wl = make_workload("BG2", 128, B, 1.5, seed=21)
+    q = wl.llr_int8()
+    bits, iters = _gpu(ldpc, wl, q, 8, early_stop=True, debug=False, threads_per_row=2)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(B, 24, replace=False))
+    idx[-1] = B - 1
+    ref = oracle.decode_layered(wl.base, wl.K_b, 128, wl.n_rows, q[idx], algo=oracle.OFFSET,
+                                max_iter=8, early_stop=True, threads=8)
+    assert np.array_equal(_unpack(ldpc, bits, wl.K)[idx], ref.bits)
+    assert np.array_equal(iters[idx], ref.iters)
+
+
+def test_low_latency_row_maps(ldpc):
+    """decode_rows through the alpha = 4 kernel: scattered pool rows in, scattered rows out."""
+    wl = make_workload("BG1", 96, 20, 1.75, seed=8)
+    q = wl.llr_int8()
+    g = ldpc.Graph(wl.base, wl.K_b, 96)
+    perm = np.random.default_rng(3).permutation(20)
+    in_rows = torch.tensor(perm[:12], dtype=torch.int32).cuda()
+    out_rows = torch.tensor(perm[8:20], dtype=torch.int32).cuda()
+    nb = (wl.K + 7) // 8
+    bits = torch.zeros((20, nb), dtype=torch.uint8, device="cuda")
+    iters = torch.full((20,), -1, dtype=torch.int32, device="cuda")
+    ldpc.decode_rows(g, torch.from_numpy(q).cuda(), in_rows, out_rows, 6, bits=bits,
+                     iters=iters, early_stop=True, threads_per_row=4)
+    torch.cuda.synchronize()
+    ref = oracle.decode_layered(wl.base, wl.K_b, 96, wl.n_rows, q[perm[:12]],
+                                algo=oracle.OFFSET, max_iter=6, early_stop=True)
+    got = ldpc.unpack_bits(bits.cpu().numpy()[perm[8:20]], wl.K)
+    assert np.array_equal(got, ref.bits)
+    assert np.array_equal(iters.cpu().numpy()[perm[8:20]], ref.iters)
+    g.close()
+
+
+def test_every_alpha_decodes_a_lone_codeword_exactly(ldpc):
+    """A lone codeword (the latency case), 10 iterations: the library's choice (0), the
+    high-throughput kernel (1) and the low-latency kernel (2, 4) all give the oracle's
+    posteriors and bits."""
+    wl = make_workload("BG1", 384, 1, 1.5, seed=9)
+    q = wl.llr_int8()
+    ref = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=10, early_stop=False, want_post=True)
+    for tpr in (0, 1, 2, 4):
+        bits, iters, post, _ = _gpu(ldpc, wl, q, 10, early_stop=False, threads_per_row=tpr)
+        assert np.array_equal(post, ref.post), tpr
+        assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits), tpr
 
 
 # ------------------------------------------------------------------ host-buffer entry point
