@@ -180,7 +180,7 @@ def profiled_traffic(kernel_tag: str):
     matches the hash recorded beside it (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_2009_05534_gb300", "csrc", "decode_tmem.cu")
+    src = os.path.join(ROOT, "paper_2009_05534_gb300", "csrc", "decode_tmem_pair.cu")
     try:
         text = open(path).read()
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

@@ -277,8 +277,8 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
             return LDPC_ERR_UNSUPPORTED;
         return launch_tmem_ll(p, A, stream);
     }
-    if (tmem_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
-        return launch_tmem(p, stream);
+    if (pair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
+        return launch_pair(p, stream);
     if (!p.in_rows && !p.out_rows && rowpair_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
         return launch_rowpair(p, p.max_deg, stream);
     if (tmem16_supported(p, llr_type, p.max_deg, (size_t)smem_optin))

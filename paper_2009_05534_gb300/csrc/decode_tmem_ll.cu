@@ -10,13 +10,15 @@
 // v2c is +127 (the largest magnitude, sign +), which changes neither the minimum, the
 // second minimum nor the sign product, and which writes nothing back.
 //
-// Arithmetic, storage and exactness follow the two-codeword TMEM kernel (decode_tmem.cu):
-// posteriors as binary16 L + 1279 in shared memory, gathered per row pair with the half
-// swap; messages as bytes c + 128 in Tensor Memory, two edge slots per 32-bit column of
-// the thread's own lane, packed tightly across rows (a thread's slots of row r follow
-// those of row r - 1); saturation of v by two relu FMAs; new magnitude
-// max(m1', (m1 + m2 - 1) - |v|).  The reduce across the A threads is exact: m1 and the
-// sign product combine by min.xorsign, and m2 = min(m2a, m2b, max(|m1a|, |m1b|)).
+// Arithmetic and exactness follow the batch kernel (decode_tmem_pair.cu): posteriors as
+// binary16 L + 1279 in shared memory, messages as bytes c + 128 in Tensor Memory,
+// saturation of v by two relu FMAs, new magnitude max(m1', (m1 + m2 - 1) - |v|).  The lanes
+// hold rows j and j + Z/2 of the one codeword (as in decode_rowpair.cu): row pair j of a
+// circulant with shift s = qH + u reads word (j + u) mod H, halves exchanged when q xor
+// wrap.  Messages: two edge slots per 32-bit column of the thread's own lane, packed
+// tightly across rows (a thread's slots of row r follow those of row r - 1).  The reduce
+// across the A threads is exact: m1 and the sign product combine by min.xorsign, and
+// m2 = min(m2a, m2b, max(|m1a|, |m1b|)).
 #include "f16x2.h"
 #include "ldpc_internal.h"
 #include "tmem.h"

@@ -1,0 +1,458 @@
+// Layered min-sum, 8-bit offset variant, with the two binary16 lanes of every register
+// carrying the same check row of two different codewords (sm_103a).  Paper: Sec. III
+// (layered min-sum with correction, stopping rule), Sec. IV (per-row m1 / m2 / sign,
+// several codewords decoded in parallel); hot-path steps a0..a6.
+//
+// Compared with a row-pair mapping (decode_rowpair.cu, decode_tmem_ll.cu), whose lanes
+// hold rows j and j + Z/2 of one codeword and must exchange the halves whenever a shift
+// wraps one row of the pair but not the other, this mapping needs no half exchange: row i
+// of a circulant with shift s reads word c*Z + (i + s) mod Z for both codewords at once, so
+// neither the gather nor the write-back permutes the halves (measured: 9 % less time per
+// iteration than the row-pair TMEM kernel it replaced).  Thread i owns check row i of every
+// layer (Z threads); two codewords per block, one block per SM.
+//
+// Why TMEM.  A BG1-shaped codeword at Z = 384 needs 52 kB of posteriors (read by every
+// check row through the circulant gather) and 124 kB of messages that only their own check
+// row ever reads.  The messages are private per row, so they live in Tensor Memory:
+// tcgen05.ld / tcgen05.st of shape 32x32b give every thread its own TMEM lane with
+// warp-uniform column indices, and the 256 kB of TMEM hold the messages of the block's
+// two codewords while shared memory holds their posteriors.
+//
+// The two codewords of a block advance in lockstep through the layers, but each lane keeps
+// its own codeword and iteration count: after every full iteration each lane applies the
+// stopping rule (or the iteration cap) on its own, writes its outputs when it stops, and is
+// refilled at once with the block's next codeword (LLRs already staged by a 1-D bulk copy),
+// which then starts its first iteration at layer 0 while the other lane carries on.  A lane
+// with no codeword left runs along without writing anything.
+//
+// Arithmetic (exact on these integers, so bit-identical to 8-bit fixed point): posteriors
+// as binary16 L + 1279 in shared memory (on [1152, 1406] binary16 has spacing 1; word
+// (c, i) holds the two codewords' values), messages as bytes c + 128 in Tensor Memory
+// (edge e at column e/2, byte 2(e%2) + lane), turned into binary16 c + 1152 by one PRMT
+// under the exponent byte 0x64, so v + 127 = (L + 1279) - (c + 1152) is one subtraction;
+// saturation of v by two relu FMAs (y = max(v + 127, 0), z = max(254 - y, 0),
+// sat(v) = 127 - z); min.xorsign.abs for m1 and the sign product, plain min / max for m2;
+// new magnitude max(m1', (m1 + m2 - 1) - |v|), which is m2' on the argmin edge and m1'
+// elsewhere, so no argmin index is kept.
+#include "f16x2.h"
+#include "ldpc_internal.h"
+#include "tmem.h"
+
+namespace ldpc {
+namespace {
+
+using namespace h2;
+using namespace tm;
+
+struct EdgeMetaQ {
+    int base;      // c*Z + s
+    int thresh;    // Z - s: rows at or above it wrap
+};
+
+constexpr int kMaxEdgesQ = 1024;
+constexpr int kMaxRowsQ = 64;
+constexpr int kTmemColsQ = 512;
+constexpr int kThreadsQ = 384;
+
+struct PairParams {
+    DecodeParams p;
+    int ncols;                   // TMEM columns per thread: ceil(E / 2)
+    int use_tma;                 // channel LLRs staged by 1-D bulk copies
+    int stage_bytes;             // per-lane staging buffer (multiple of 16)
+    int off_lb, off_stage;       // shared-memory offsets of the posteriors and the staging
+    int row[kMaxRowsQ + 1];      // edge offsets of the rows
+    EdgeMetaQ meta[kMaxEdgesQ];
+};
+
+// --------------------------------------------------------------------------- one layer
+
+// Thread i processes check row i (both lanes) of a layer of degree D whose first edge sits
+// in the upper half of its TMEM column when P = 1.
+template <int D, int P>
+__device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, uint32_t *Lb, uint32_t tcolumn,
+                                       int e0, int Z, int i, bool store) {
+    constexpr int NC = (P + D + 1) / 2;
+    uint32_t cm[NC];
+    twait_st();
+    tload<NC>(tcolumn, cm);
+    uint32_t X[D];
+    int addr[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const EdgeMetaQ mt = meta[e0 + j];
+        addr[j] = i + mt.base - (i >= mt.thresh ? Z : 0);
+        X[j] = Lb[addr[j]];
+    }
+    twait_ld();
+    uint32_t m1 = kInf2, m2 = kInf2;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const uint32_t M =
+            prmt(cm[(P + j) >> 1], 0x64646464u, ((P + j) & 1) ? 0x4342u : 0x4140u);
+        const uint32_t y = h2relu_fma(M, kNegOne2, X[j]);   // max(v + 127, 0)
+        const uint32_t z = h2relu_fma(y, kNegOne2, k254);   // max(254 - y, 0)
+        const uint32_t x = h2sub(kP127, z);                 // sat(v)
+        m2 = h2min(m2, h2max(h2abs(m1), h2abs(x)));
+        m1 = h2minxs(m1, x);
+        X[j] = x;
+    }
+    const uint32_t SO = (m1 & kSign2) | kOne2;
+    const uint32_t a1 = m1 & kAbs2, a2 = m2 & kAbs2;
+    const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);
+    const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);
+    uint32_t C[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const uint32_t x = X[j];
+        const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
+        const uint32_t sg = (x & kSign2) ^ SO;
+        C[j] = h2fma(ex, sg, kBias2);                          // c' + 1152
+        uint32_t L = h2add(C[j], h2add(x, kP127));             // (x + c') + 1279
+        L = h2max(h2min(L, kPostHi), kPostLo);
+        if (store) Lb[addr[j]] = L;
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int jl = 2 * k - P, jh = 2 * k + 1 - P;
+        const int il = jl < 0 ? 0 : jl, ih = jh >= D ? D - 1 : jh;
+        if (jl >= 0 && jh < D)
+            cm[k] = prmt(C[il], C[ih], 0x6420u);
+        else if (jl >= 0)
+            cm[k] = prmt(C[il], cm[k], 0x7620u);
+        else
+            cm[k] = prmt(cm[k], C[ih], 0x6410u);
+    }
+    tstore<NC>(tcolumn, cm);
+}
+
+template <int D>
+__device__ __forceinline__ void pq_row_any(const EdgeMetaQ *meta, uint32_t *Lb, uint32_t tbase,
+                                           int e0, int Z, int i, bool store) {
+    if (e0 & 1)
+        pq_row<D, 1>(meta, Lb, tbase + (uint32_t)(e0 >> 1), e0, Z, i, store);
+    else
+        pq_row<D, 0>(meta, Lb, tbase + (uint32_t)(e0 >> 1), e0, Z, i, store);
+}
+
+__device__ __forceinline__ void pq_dispatch(int d, const EdgeMetaQ *meta, uint32_t *Lb,
+                                            uint32_t tbase, int e0, int Z, int i, bool store) {
+    switch (d) {
+#define LDPC_PQ_CASE(D) \
+    case D:             \
+        pq_row_any<D>(meta, Lb, tbase, e0, Z, i, store); \
+        break;
+        LDPC_PQ_CASE(2) LDPC_PQ_CASE(3) LDPC_PQ_CASE(4) LDPC_PQ_CASE(5) LDPC_PQ_CASE(6)
+        LDPC_PQ_CASE(7) LDPC_PQ_CASE(8) LDPC_PQ_CASE(9) LDPC_PQ_CASE(10) LDPC_PQ_CASE(11)
+        LDPC_PQ_CASE(12) LDPC_PQ_CASE(13) LDPC_PQ_CASE(14) LDPC_PQ_CASE(15) LDPC_PQ_CASE(16)
+        LDPC_PQ_CASE(17) LDPC_PQ_CASE(18) LDPC_PQ_CASE(19) LDPC_PQ_CASE(20)
+#undef LDPC_PQ_CASE
+    default:
+        break;
+    }
+}
+
+// parity masks of check row i over a row's edges: 0xFFFF in a lane whose codeword has an
+// odd number of negative posteriors on the row
+__device__ __forceinline__ uint32_t pq_parity(const EdgeMetaQ *meta, const uint32_t *Lb, int e0,
+                                              int d, int Z, int i) {
+    uint32_t par = 0;
+    for (int j = 0; j < d; ++j) {
+        const EdgeMetaQ mt = meta[e0 + j];
+        par ^= h2lt_mask(Lb[i + mt.base - (i >= mt.thresh ? Z : 0)], kPostBias);
+    }
+    return par;
+}
+
+// ---------------------------------------------------------------------------- the kernel
+
+__global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constant__ PairParams pp) {
+    const DecodeParams &p = pp.p;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tmem_base;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_bad[2];
+    const int Z = p.Z, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
+    const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x;
+    const bool store = tid < Z;
+    const int i = store ? tid : Z - 1;                // spare threads shadow the last row
+    // shared memory: edge metadata | posterior words | two LLR staging buffers
+    EdgeMetaQ *s_meta = reinterpret_cast<EdgeMetaQ *>(smem);
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem + pp.off_lb);
+    uint16_t *Lh = reinterpret_cast<uint16_t *>(smem + pp.off_lb);   // lane X of word j: Lh[2j + X]
+    int8_t *stage = reinterpret_cast<int8_t *>(smem + pp.off_stage);
+
+    for (int e = tid; e < E; e += nthr) s_meta[e] = pp.meta[e];
+    if (tid == 0) {
+        if (pp.use_tma) {
+            mbar_init(&s_bar[0]);
+            mbar_init(&s_bar[1]);
+        }
+        s_bad[0] = s_bad[1] = 0u;
+    }
+    if (warp == 0) tmem_alloc(&s_tmem_base, kTmemColsQ);
+    tmem_block_sync();
+    const uint32_t tbase = s_tmem_base + ((uint32_t)((warp & 3) * 32) << 16) +
+                           (uint32_t)((warp >> 2) * pp.ncols);
+
+    const int K = p.K_b * Z;
+    const int nbytes = (K + 7) >> 3;
+    const int lo = p.punct * Z;
+    const int NV = n_cols * Z;
+    const int8_t *llr_all = reinterpret_cast<const int8_t *>(p.llr);
+    // Work distribution: codewords are claimed one at a time from a counter shared by the
+    // blocks of the launch (p.queue[0]), so a block whose codewords stop early takes more
+    // of them; without a counter block b takes b, b + G, b + 2G, ...  A claim is staged at
+    // once in one of the two buffers, and the block holds at most one claimed codeword that
+    // no lane has started.  Every thread keeps the same copy of this state.
+    __shared__ int s_claim[2];
+    int cw[2] = {-1, -1}, t[2] = {0, 0}, buf[2] = {0, 1};
+    int staged = -1, sbuf = 0, lastb = 1, n_claims = 0;
+    bool drained = false;
+    uint32_t parity = 0u;                // bit S: phase parity of staging buffer S
+    uint32_t pending = 0u;               // bit S: a copy into buffer S issued, not consumed
+    bool failed = false;
+    // thread 0 claims the next codeword and starts its copy into buffer S (free: no thread
+    // reads it); every thread gets the codeword, or -1 once the batch is exhausted
+    auto claim = [&](int S) -> int {
+        if (drained) return -1;
+        const int slot = n_claims & 1;   // two slots: one barrier per claim suffices
+        ++n_claims;
+        if (tid == 0) {
+            const int k = p.queue ? atomicAdd(p.queue, 1)
+                                  : (int)blockIdx.x + (n_claims - 1) * (int)gridDim.x;
+            const int c = k < p.batch ? k : -1;
+            s_claim[slot] = c;
+            if (c >= 0 && pp.use_tma)
+                bulk_load(stage + S * pp.stage_bytes, llr_all + in_row(p, c) * p.n_tx,
+                          (uint32_t)p.n_tx, &s_bar[S]);
+        }
+        named_sync(1, nthr);
+        const int c = s_claim[slot];
+        if (c < 0)
+            drained = true;
+        else if (pp.use_tma)
+            pending |= 1u << S;
+        return c;
+    };
+    // a0 for lane X: its messages to zero (byte 0x80), its posteriors from the channel
+    // LLRs; false (for every thread) if the staged copy timed out
+    auto init_lane = [&](int X) -> bool {
+        const uint32_t keep = X ? 0x00FF00FFu : 0xFF00FF00u;
+        const uint32_t set = X ? 0x80008000u : 0x00800080u;
+        twait_st();
+        int c = 0;
+        for (; c + 16 <= pp.ncols; c += 16) {
+            uint32_t v[16];
+            tld<16>(tbase + c, v);
+            twait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = (v[q] & keep) | set;
+            tst<16>(tbase + c, v);
+        }
+        for (; c < pp.ncols; ++c) {
+            uint32_t v;
+            tld<1>(tbase + c, &v);
+            twait_ld();
+            v = (v & keep) | set;
+            tst<1>(tbase + c, &v);
+        }
+        const int8_t *src = llr_all + in_row(p, cw[X]) * p.n_tx;
+        if (pp.use_tma) {
+            const int S = buf[X];
+            const bool ok = mbar_wait(&s_bar[S], (parity >> S) & 1u);
+            if (named_or(1, nthr, !ok)) {
+                if (tid == 0) atomicCAS(p.status, 0, (int)LDPC_ERR_TIMEOUT);
+                return false;                // parity stays on the copy still in flight
+            }
+            parity ^= 1u << S;
+            pending &= ~(1u << S);
+            src = stage + S * pp.stage_bytes;
+        }
+        // binary16 L + 1279 = 1024 + (L + 255): bit pattern 0x6400 + L + 255
+        for (int j = tid; j < NV; j += nthr) {
+            const int t0 = j - lo;
+            const int q = (t0 >= 0 && t0 < p.n_tx) ? (int)src[t0] : 0;
+            Lh[2 * j + X] = (uint16_t)(0x64FF + q);
+        }
+        return true;
+    };
+    // a6 for lane X: hard bits, iteration count, and the debug outputs
+    auto emit = [&](int X) {
+        for (int b = tid; b < nbytes; b += nthr) {
+            unsigned x = 0;
+            for (int kk = 0; kk < 8; ++kk) {
+                const int j = 8 * b + kk;
+                if (j >= K) break;
+                if (Lh[2 * j + X] < 0x64FFu) x |= 1u << kk;
+            }
+            p.bits[out_row(p, cw[X]) * nbytes + b] = (uint8_t)x;
+        }
+        if (tid == 0) p.iters[out_row(p, cw[X])] = t[X];
+        if (p.post) {
+            int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw[X] * NV;
+            for (int j = tid; j < NV; j += nthr) po[j] = (int8_t)((int)Lh[2 * j + X] - 0x64FF);
+        }
+        if (p.c2v) {
+            twait_st();
+            int8_t *co = reinterpret_cast<int8_t *>(p.c2v) + (size_t)cw[X] * E * Z;
+            for (int e = 0; e < E; ++e) {
+                uint32_t v;
+                tld<1>(tbase + (uint32_t)(e >> 1), &v);
+                twait_ld();
+                const uint32_t byte = (v >> (8 * (2 * (e & 1) + X))) & 0xffu;
+                if (store) co[(size_t)e * Z + i] = (int8_t)(uint8_t)(byte ^ 0x80u);
+            }
+        }
+    };
+
+    cw[0] = claim(0);
+    cw[1] = claim(1);
+#pragma unroll
+    for (int X = 0; X < 2 && !failed; ++X)
+        if (cw[X] >= 0) failed = !init_lane(X);
+    named_sync(1, nthr);                             // buffer 0 free again
+    if (!failed) {
+        sbuf = 0;
+        staged = claim(sbuf);
+    }
+
+    int ib = 0;                                      // iterations run by the block
+#pragma unroll 1
+    while (!failed && (cw[0] >= 0 || cw[1] >= 0)) {
+#pragma unroll 1
+        for (int r = 0; r < n_rows; ++r) {
+            const int e0 = pp.row[r];
+            pq_dispatch(pp.row[r + 1] - e0, s_meta, Lb, tbase, e0, Z, i, store);
+            named_sync(1, nthr);
+        }
+        ++t[0];
+        ++t[1];
+        // a5: the stopping rule per lane (bits 0..15: lane 0, 16..31: lane 1); a lane with
+        // no codeword counts as failing so that the scan can end early
+        uint32_t bad = 0xFFFFFFFFu;
+        if (p.early_stop) {
+            const int sb = ib & 1;
+            uint32_t acc = (cw[0] < 0 ? 0x0000FFFFu : 0u) | (cw[1] < 0 ? 0xFFFF0000u : 0u);
+            for (int r = 0; r < n_rows && __reduce_or_sync(0xffffffffu, acc) != 0xFFFFFFFFu;
+                 ++r) {
+                const int e0 = pp.row[r];
+                acc |= pq_parity(s_meta, Lb, e0, pp.row[r + 1] - e0, Z, i);
+            }
+            acc = __reduce_or_sync(0xffffffffu, acc);
+            if ((tid & 31) == 0 && acc) atomicOr(&s_bad[sb], acc);
+            named_sync(1, nthr);
+            bad = s_bad[sb];
+            if (tid == 0) s_bad[sb ^ 1] = 0u;        // read by everyone one iteration ago
+        }
+        ++ib;
+        bool done[2];
+#pragma unroll
+        for (int X = 0; X < 2; ++X)
+            done[X] = cw[X] >= 0 &&
+                      (t[X] >= p.max_iter || ((bad >> (16 * X)) & 0xFFFFu) == 0u);
+        if (!done[0] && !done[1]) continue;
+#pragma unroll
+        for (int X = 0; X < 2; ++X)
+            if (done[X]) emit(X);
+        named_sync(1, nthr);                         // outputs read before the refill
+#pragma unroll
+        for (int X = 0; X < 2 && !failed; ++X) {
+            if (!done[X]) continue;
+            int b;
+            if (staged >= 0) {
+                cw[X] = staged;
+                b = sbuf;
+                staged = -1;
+            } else {
+                b = lastb ^ 1;                       // the other buffer may still be read
+                cw[X] = claim(b);
+            }
+            lastb = b;
+            buf[X] = b;
+            t[X] = 0;
+            if (cw[X] >= 0) failed = !init_lane(X);
+        }
+        named_sync(1, nthr);                         // refilled posteriors visible; staging free
+        if (!failed && staged < 0) {
+            sbuf = lastb ^ 1;
+            staged = claim(sbuf);
+        }
+    }
+    // a copy still in flight after a timeout must not outlive the block (bounded waits)
+    if (failed && tid == 0)
+#pragma unroll
+        for (int S = 0; S < 2; ++S)
+            if ((pending >> S) & 1u) mbar_wait(&s_bar[S], (parity >> S) & 1u);
+
+    // the last block of the launch to finish resets the shared counter for the next launch
+    // on this stream
+    if (p.queue && tid == 0) {
+        __threadfence();
+        if (atomicAdd(p.queue + 1, 1) == (int)gridDim.x - 1) {
+            p.queue[0] = 0;
+            p.queue[1] = 0;
+        }
+    }
+
+    tmem_block_sync();
+    if (warp == 0) tmem_dealloc(s_tmem_base, kTmemColsQ);
+}
+
+size_t pair_smem_bytes(const DecodeParams &p, bool tma, int *off_lb, int *off_stage,
+                       int *stage_bytes) {
+    const int lb = (int)(((size_t)p.E * sizeof(EdgeMetaQ) + 15) & ~(size_t)15);
+    const int st = (int)((lb + (size_t)p.n_cols * p.Z * 4 + 15) & ~(size_t)15);
+    const int sb = tma ? ((p.n_tx + 15) & ~15) : 0;
+    if (off_lb) *off_lb = lb;
+    if (off_stage) *off_stage = st;
+    if (stage_bytes) *stage_bytes = sb;
+    return (size_t)st + 2 * (size_t)sb;
+}
+
+}  // namespace
+
+bool pair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin) {
+    if (llr_type != LDPC_LLR_INT8 || p.algo != LDPC_OFFSET || p.offset_q != 1) return false;
+    if (p.Z < 1 || p.Z > kThreadsQ || max_deg > kMaxDeg || max_deg < 2) return false;
+    if (p.E > kMaxEdgesQ || p.n_rows > kMaxRowsQ) return false;
+    const int nwarps = (p.Z + 31) / 32;
+    const int depth = (nwarps + 3) / 4;
+    if (depth * ((p.E + 1) / 2) > kTmemColsQ) return false;
+    return pair_smem_bytes(p, true, nullptr, nullptr, nullptr) + 64 <= smem_optin;
+}
+
+ldpc_status launch_pair(const DecodeParams &p, cudaStream_t stream) {
+    static thread_local PairParams pp;     // ~10 kB: kept off the stack
+    pp.p = p;
+    for (int r = 0; r <= p.n_rows; ++r) pp.row[r] = p.h_row_ptr[r];
+    pp.ncols = (p.E + 1) / 2;
+    for (int e = 0; e < p.E; ++e) {
+        const uint32_t ed = p.h_edges[e];
+        const int c = (int)(ed >> 16), s = (int)(ed & 0xffffu);
+        pp.meta[e].base = c * p.Z + s;
+        pp.meta[e].thresh = p.Z - s;
+    }
+    // bulk copies need 16-byte aligned rows; at least 120 kB of shared memory so that one
+    // block occupies the SM (its TMEM allocation takes all 512 columns)
+    pp.use_tma = ((reinterpret_cast<uintptr_t>(p.llr) & 15u) == 0 && (p.n_tx % 16) == 0 &&
+                  p.n_tx > 0 && p.n_tx < (1 << 20))
+                     ? 1
+                     : 0;
+    size_t smem = pair_smem_bytes(p, pp.use_tma != 0, &pp.off_lb, &pp.off_stage, &pp.stage_bytes);
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    const int threads = ((p.Z + 31) / 32) * 32;
+    int grid = (p.batch + 1) / 2;
+    if (grid > n_sm) grid = n_sm;
+    pair_kernel<<<grid, threads, smem, stream>>>(pp);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+}  // namespace ldpc

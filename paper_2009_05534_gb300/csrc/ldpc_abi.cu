@@ -30,6 +30,15 @@ struct ListWorkspace {
 static std::mutex g_ws_mu;
 static std::map<std::pair<int, cudaStream_t>, ListWorkspace> g_ws;
 
+int *graph_queue(Graph *g, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lk(g->q_mu);
+    for (int k = 0; k < g->n_queues; ++k)
+        if (g->q_stream[k] == stream) return g->d_queues + 2 * k;
+    if (g->n_queues == Graph::kQueues) return nullptr;
+    g->q_stream[g->n_queues] = stream;
+    return g->d_queues + 2 * g->n_queues++;
+}
+
 }  // namespace ldpc
 
 using ldpc::Graph;
@@ -110,15 +119,18 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
     g->min_deg_upto[M_bg] = mind;
     cudaGetDevice(&g->device);
     ldpc_status st = LDPC_OK;
+    const size_t q_bytes = sizeof(int) * 2 * Graph::kQueues;
     if (cudaMalloc(&g->d_edges, sizeof(uint32_t) * E) != cudaSuccess ||
         cudaMalloc(&g->d_row_ptr, sizeof(int) * (M_bg + 1)) != cudaSuccess ||
-        cudaMalloc(&g->d_status, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&g->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&g->d_queues, q_bytes) != cudaSuccess) {
         st = LDPC_ERR_OUT_OF_MEMORY;
     } else if (cudaMemcpy(g->d_edges, h_edges, sizeof(uint32_t) * E, cudaMemcpyHostToDevice) !=
                    cudaSuccess ||
                cudaMemcpy(g->d_row_ptr, g->row_ptr, sizeof(int) * (M_bg + 1),
                           cudaMemcpyHostToDevice) != cudaSuccess ||
-               cudaMemset(g->d_status, 0, sizeof(int)) != cudaSuccess) {
+               cudaMemset(g->d_status, 0, sizeof(int)) != cudaSuccess ||
+               cudaMemset(g->d_queues, 0, q_bytes) != cudaSuccess) {
         st = LDPC_ERR_CUDA;
     }
     if (st != LDPC_OK) {
@@ -126,6 +138,7 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
         cudaFree(g->d_edges);
         cudaFree(g->d_row_ptr);
         cudaFree(g->d_status);
+        cudaFree(g->d_queues);
         delete g;
         return st;
     }
@@ -140,6 +153,7 @@ ldpc_status ldpc_graph_destroy(ldpc_graph_t h) {
     cudaFree(g->d_edges);
     cudaFree(g->d_row_ptr);
     cudaFree(g->d_status);
+    cudaFree(g->d_queues);
     cudaFree(g->d_stage);
     for (int k = 0; k < Graph::kHostChunks; ++k)
         if (g->chunk_ev[k]) cudaEventDestroy(g->chunk_ev[k]);
@@ -242,6 +256,7 @@ static ldpc_status decode_params(ldpc_graph_t h, const void *llr, int batch, int
     p.in_rows = nullptr;
     p.out_rows = nullptr;
     p.threads_per_row = o.threads_per_row;
+    p.queue = nullptr;
     *o_out = o;
     return LDPC_OK;
 }
@@ -255,6 +270,7 @@ static ldpc_status decode_common(ldpc_graph_t h, const void *llr, int batch, int
     const ldpc_status st = decode_params(h, llr, batch, max_iter, opts, bits, iters, post, c2v,
                                          false, &p, &o, &empty);
     if (st != LDPC_OK || empty) return st;
+    p.queue = ldpc::graph_queue(reinterpret_cast<Graph *>(h), reinterpret_cast<cudaStream_t>(stream));
     return ldpc::launch_layered(p, o.llr_type, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -278,6 +294,7 @@ ldpc_status ldpc_decode_rows(ldpc_graph_t g, const void *llr_dev, const int32_t 
     if (!in_rows_dev || !out_rows_dev) return LDPC_ERR_INVALID_ARG;
     p.in_rows = in_rows_dev;
     p.out_rows = out_rows_dev;
+    p.queue = ldpc::graph_queue(reinterpret_cast<Graph *>(g), reinterpret_cast<cudaStream_t>(stream));
     return ldpc::launch_layered(p, o.llr_type, reinterpret_cast<cudaStream_t>(stream));
 }
 

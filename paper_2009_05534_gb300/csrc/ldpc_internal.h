@@ -36,7 +36,18 @@ struct Graph {
     cudaStream_t copy_stream = nullptr;
     static constexpr int kHostChunks = 16;
     cudaEvent_t chunk_ev[kHostChunks] = {};
+    // work counters of the batch kernel: one pair per stream that decodes with the graph
+    // (zero between launches; the last block of a launch resets its pair)
+    static constexpr int kQueues = 64;
+    std::mutex q_mu;
+    int *d_queues = nullptr;              // device [kQueues][2]
+    cudaStream_t q_stream[kQueues] = {};
+    int n_queues = 0;
 };
+
+// The work-counter pair of `g` for decodes on `stream`, or null when every slot is taken
+// (the kernel then falls back to a fixed assignment of codewords to blocks).
+int *graph_queue(Graph *g, cudaStream_t stream);
 
 // Everything a decode kernel needs, passed by value.
 struct DecodeParams {
@@ -60,6 +71,7 @@ struct DecodeParams {
     const int32_t *in_rows;   // [batch] LLR row of codeword b, or null (row b)
     const int32_t *out_rows;  // [batch] output row of codeword b, or null (row b)
     int threads_per_row;      // cooperating threads per row pair (0 = automatic)
+    int *queue;               // device [2] work counters of the launch's stream, or null
 };
 
 // source and destination rows of codeword b of a batch (identity without row maps)
@@ -85,9 +97,10 @@ struct ListItem {
 // found while configuring the launch.
 ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t stream);
 
-// Two-codeword row-pair kernel with messages in Tensor Memory (decode_tmem.cu).
-bool tmem_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
-ldpc_status launch_tmem(const DecodeParams &p, cudaStream_t stream);
+// Two codewords per thread (one per binary16 lane), one check row per thread, messages in
+// Tensor Memory, per-lane stopping and refill (decode_tmem_pair.cu).
+bool pair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
+ldpc_status launch_pair(const DecodeParams &p, cudaStream_t stream);
 
 // One-codeword kernel with A = 2 or 4 cooperating threads per row pair, messages in
 // Tensor Memory (decode_tmem_ll.cu): the low-latency strategy.

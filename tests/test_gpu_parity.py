@@ -293,6 +293,62 @@ def test_int8_dense_bg1_table_z384(ldpc, tpr):
     g.close()
 
 
+# ------------------------------------- batch kernel: work counter, lane refill, streams
+
+def test_batch_kernel_many_codewords_per_block_early_stop(ldpc):
+    """Several codewords per block with varied iteration counts: lanes stop on their own,
+    take the next codeword from the launch's work counter and start it at layer 0 while
+    the other lane carries on; every codeword's bits and iteration count match the oracle,
+    in three consecutive launches on one stream (the counter resets itself)."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    B = 6 * n_sm + 11
+    wl = make_workload("BG1", 40, B, 1.25, seed=23)
+    q = wl.llr_int8()
+    ref = oracle.decode_layered(wl.base, wl.K_b, 40, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=10, early_stop=True, threads=8)
+    assert len(np.unique(ref.iters)) >= 4               # the stopping rule is exercised
+    g = ldpc.Graph(wl.base, wl.K_b, 40)
+    t = torch.from_numpy(q).cuda()
+    s = torch.cuda.Stream()
+    nb = (wl.K + 7) // 8
+    for rep in range(3):
+        bits = torch.full((B, nb), 0xAB, dtype=torch.uint8, device="cuda")
+        iters = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()                        # the fills ran on another stream
+        ldpc.decode(g, t, 10, early_stop=True, stream=s, bits=bits, iters=iters,
+                    threads_per_row=1)
+        torch.cuda.synchronize()
+        assert np.array_equal(iters.cpu().numpy(), ref.iters), rep
+        assert np.array_equal(_unpack(ldpc, bits.cpu().numpy(), wl.K), ref.bits), rep
+    g.sync_status()
+    g.close()
+
+
+def test_batch_kernel_two_streams_share_a_graph(ldpc):
+    """Decodes of one graph launched on two streams without a sync between them use
+    separate work counters; both match the oracle."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    B = 3 * n_sm
+    wl = make_workload("BG2", 96, 2 * B, 1.0, seed=29)
+    q = wl.llr_int8()
+    ref = oracle.decode_layered(wl.base, wl.K_b, 96, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=8, early_stop=True, threads=8)
+    g = ldpc.Graph(wl.base, wl.K_b, 96)
+    t = torch.from_numpy(q).cuda()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    outs = []
+    for k, s in enumerate(streams):
+        outs.append(ldpc.decode(g, t[k * B:(k + 1) * B], 8, early_stop=True, stream=s,
+                                threads_per_row=1))
+    torch.cuda.synchronize()
+    for k, (bits, iters) in enumerate(outs):
+        sl = slice(k * B, (k + 1) * B)
+        assert np.array_equal(iters.cpu().numpy(), ref.iters[sl]), k
+        assert np.array_equal(_unpack(ldpc, bits.cpu().numpy(), wl.K), ref.bits[sl]), k
+    g.close()
+
+
 # ------------------------------------------------- low-latency strategy (alpha threads)
 
 def test_low_latency_batch_beyond_sm_count(ldpc):
