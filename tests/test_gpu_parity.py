@@ -349,6 +349,28 @@ def test_batch_kernel_two_streams_share_a_graph(ldpc):
     g.close()
 
 
+def test_batch_kernel_more_streams_than_counters(ldpc):
+    """A graph has 64 work-counter pairs; decodes on further streams fall back to a fixed
+    assignment of codewords to blocks and stay exact."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    B = n_sm + 9                                   # beyond the low-latency range
+    wl = make_workload("BG2", 32, B, 1.5, seed=31)
+    q = wl.llr_int8()
+    ref = oracle.decode_layered(wl.base, wl.K_b, 32, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=6, early_stop=True, threads=8)
+    g = ldpc.Graph(wl.base, wl.K_b, 32)
+    t = torch.from_numpy(q).cuda()
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(70)]
+    for k, s in enumerate(streams):
+        bits, iters = ldpc.decode(g, t, 6, early_stop=True, stream=s, threads_per_row=1)
+        s.synchronize()
+        if k in (0, 63, 64, 69):
+            assert np.array_equal(iters.cpu().numpy(), ref.iters), k
+            assert np.array_equal(_unpack(ldpc, bits.cpu().numpy(), wl.K), ref.bits), k
+    g.close()
+
+
 # ------------------------------------------------- low-latency strategy (alpha threads)
 
 def test_low_latency_batch_beyond_sm_count(ldpc):
