@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
     }
 
     int ib = 0;                                      // iterations run by the block
+    int r_scan = 0;                                  // first layer of this warp's next scan
 #pragma unroll 1
     while (!failed && (cw[0] >= 0 || cw[1] >= 0)) {
 #pragma unroll 1
@@ -328,20 +329,33 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
         ++t[0];
         ++t[1];
         // a5: the stopping rule per lane (bits 0..15: lane 0, 16..31: lane 1); a lane with
-        // no codeword counts as failing so that the scan can end early
+        // no codeword counts as failing.  The scan ends block-wide: each warp publishes the
+        // failing-lane bits it finds, and every warp stops once the block's bits show both
+        // lanes failing (neither lane is done, whatever the other rows say); only a lane
+        // that satisfies every check needs the whole scan.  Each warp starts at the layer
+        // where it last found a failing check (the order does not change the result).
         uint32_t bad = 0xFFFFFFFFu;
         if (p.early_stop) {
             const int sb = ib & 1;
-            uint32_t acc = (cw[0] < 0 ? 0x0000FFFFu : 0u) | (cw[1] < 0 ? 0xFFFF0000u : 0u);
-            for (int r = 0; r < n_rows && __reduce_or_sync(0xffffffffu, acc) != 0xFFFFFFFFu;
-                 ++r) {
+            const uint32_t ghost = (cw[0] < 0 ? 0x0000FFFFu : 0u) | (cw[1] < 0 ? 0xFFFF0000u : 0u);
+            volatile uint32_t *vbad = &s_bad[sb];
+            uint32_t acc = ghost, seen = ghost;
+            int r = r_scan;
+            for (int k = 0; k < n_rows; ++k, r = (r + 1 == n_rows) ? 0 : r + 1) {
+                const uint32_t wacc = __reduce_or_sync(0xffffffffu, acc);
+                if (wacc != seen) {                  // new failing lanes: publish them
+                    if ((tid & 31) == 0) atomicOr(&s_bad[sb], wacc);
+                    if (seen == ghost) r_scan = r == 0 ? n_rows - 1 : r - 1;
+                    seen = wacc;
+                }
+                if ((wacc | *vbad) == 0xFFFFFFFFu) break;
                 const int e0 = pp.row[r];
                 acc |= pq_parity(s_meta, Lb, e0, pp.row[r + 1] - e0, Z, i);
             }
-            acc = __reduce_or_sync(0xffffffffu, acc);
-            if ((tid & 31) == 0 && acc) atomicOr(&s_bad[sb], acc);
+            const uint32_t wacc = __reduce_or_sync(0xffffffffu, acc);
+            if ((tid & 31) == 0 && wacc != seen) atomicOr(&s_bad[sb], wacc);
             named_sync(1, nthr);
-            bad = s_bad[sb];
+            bad = s_bad[sb] | ghost;
             if (tid == 0) s_bad[sb ^ 1] = 0u;        // read by everyone one iteration ago
         }
         ++ib;
