@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tmem_base;
     __shared__ __align__(8) uint64_t s_bar[kCw];
+    __shared__ int s_stop[kCw][2];                    // per codeword: a failing check found
     const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nthr_half = pp.wpc * 32;
@@ -265,6 +266,8 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
                               llr_all + in_row(p, cw + stride) * p.n_tx,
                               (uint32_t)(2 * p.n_tx), bar);
 
+                if (ht == 0) s_stop[half][0] = s_stop[half][1] = 0;   // published by a barrier
+                int r_scan = 0;                      // first layer of this warp's next scan
                 int done = p.max_iter;
 #pragma unroll 1
                 for (int t = 1; t <= p.max_iter; ++t) {
@@ -286,12 +289,23 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
                         named_sync(bar_id, nthr_half);
                     }
                     if (p.early_stop) {
-                        int bad = 0;
-                        for (int r = 0; r < n_rows && !bad; ++r) {
+                        // block-wide exit within the codeword's half: the first warp to find
+                        // a failing check raises its flag and every warp of the half stops;
+                        // each warp starts at its last failing layer
+                        volatile int *vstop = &s_stop[half][t & 1];
+                        int bad = 0, r = r_scan;
+                        for (int q = 0; q < n_rows && !bad && !*vstop;
+                             ++q, r = (r + 1 == n_rows) ? 0 : r + 1) {
                             const int e0 = pp.row[r], d = pp.row[r + 1] - e0;
                             bad = __any_sync(0xffffffffu, parity16(s_meta, Lb, e0, d, H, w) != 0u);
+                            if (bad) {
+                                if ((tid & 31) == 0) *vstop = 1;
+                                r_scan = r;
+                            }
                         }
-                        if (named_or(bar_id, nthr_half, bad) == 0) {
+                        const int any = named_or(bar_id, nthr_half, bad);
+                        if (ht == 0) s_stop[half][(t + 1) & 1] = 0;   // read an iteration ago
+                        if (any == 0) {
                             done = t;
                             break;
                         }

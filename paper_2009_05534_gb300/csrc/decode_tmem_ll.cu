@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(A * 192, 1) tmem_ll_kernel(const __grid_consta
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tmem_base;
     __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_stop[2];                         // a failing check found (per iteration parity)
     const int Z = p.Z, H = pp.H, E = p.E, n_rows = p.n_rows, n_cols = p.n_cols;
     const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x;
     const int k = tid % A;                            // cooperating thread of the row pair
@@ -245,6 +246,8 @@ __global__ void __launch_bounds__(A * 192, 1) tmem_ll_kernel(const __grid_consta
             bulk_load(const_cast<int8_t *>(stage),
                       llr_all + in_row(p, cw + gridDim.x) * p.n_tx, (uint32_t)p.n_tx, bar);
 
+        if (tid == 0) s_stop[0] = s_stop[1] = 0;     // published by the first layer barrier
+        int r_scan = 0;                              // first layer of this warp's next scan
         int done = p.max_iter;
 #pragma unroll 1
         for (int t = 1; t <= p.max_iter; ++t) {
@@ -256,13 +259,23 @@ __global__ void __launch_bounds__(A * 192, 1) tmem_ll_kernel(const __grid_consta
                 named_sync(1, nthr);
             }
             if (p.early_stop) {
-                int bad = 0;
-                for (int r = 0; r < n_rows && !bad; ++r) {
+                // block-wide exit: the first warp to find a failing check raises
+                // s_stop[t & 1] and every warp stops; each starts at its last failing layer
+                volatile int *vstop = &s_stop[t & 1];
+                int bad = 0, r = r_scan;
+                for (int q = 0; q < n_rows && !bad && !*vstop;
+                     ++q, r = (r + 1 == n_rows) ? 0 : r + 1) {
                     const int e0 = pp.row[r];
                     bad = __any_sync(0xffffffffu, ll_parity<A>(s_meta, Lb, e0,
                                                                 pp.row[r + 1] - e0, H, w, k) != 0u);
+                    if (bad) {
+                        if ((tid & 31) == 0) *vstop = 1;
+                        r_scan = r;
+                    }
                 }
-                if (named_or(1, nthr, bad) == 0) {
+                const int any = named_or(1, nthr, bad);
+                if (tid == 0) s_stop[(t + 1) & 1] = 0;  // read by everyone an iteration ago
+                if (any == 0) {
                     done = t;
                     break;
                 }
