@@ -362,13 +362,27 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
     int dev = 0, n_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    int chunk = 2 * n_sm;
-    if ((batch + chunk - 1) / chunk > Graph::kHostChunks)
-        chunk = (batch + Graph::kHostChunks - 1) / Graph::kHostChunks;
-    const int n_chunks = (batch + chunk - 1) / chunk;
+    // chunk k covers codewords [start[k], start[k + 1]); for int8 the first chunk is one
+    // codeword per SM (decoded by the low-latency kernel in about the time of a full
+    // round), which halves the upload that nothing overlaps
+    int start[Graph::kHostChunks + 1];
+    int n_chunks = 0;
+    {
+        int chunk = 2 * n_sm;
+        int first = (o.llr_type == LDPC_LLR_INT8 && batch > 2 * n_sm) ? n_sm : chunk;
+        if (1 + (batch - first + chunk - 1) / chunk > Graph::kHostChunks) {
+            chunk = (batch + Graph::kHostChunks - 1) / Graph::kHostChunks;
+            first = chunk;
+        }
+        start[0] = 0;
+        for (int b = first < batch ? first : batch;; b = b + chunk < batch ? b + chunk : batch) {
+            start[++n_chunks] = b;
+            if (b == batch) break;
+        }
+    }
     for (int k = 0; k < n_chunks; ++k) {
-        const size_t b0 = (size_t)k * chunk;
-        const size_t nb = (size_t)(batch - (int)b0 < chunk ? batch - (int)b0 : chunk);
+        const size_t b0 = (size_t)start[k];
+        const size_t nb = (size_t)(start[k + 1] - start[k]);
         if (cudaMemcpyAsync(d_llr + b0 * n_tx * esz, (const char *)llr_host + b0 * n_tx * esz,
                             nb * n_tx * esz, cudaMemcpyHostToDevice,
                             g->copy_stream) != cudaSuccess ||
@@ -376,8 +390,8 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
             return LDPC_ERR_CUDA;
     }
     for (int k = 0; k < n_chunks; ++k) {
-        const size_t b0 = (size_t)k * chunk;
-        const int nb = batch - (int)b0 < chunk ? batch - (int)b0 : chunk;
+        const size_t b0 = (size_t)start[k];
+        const int nb = start[k + 1] - start[k];
         if (cudaStreamWaitEvent(s, g->chunk_ev[k], 0) != cudaSuccess) return LDPC_ERR_CUDA;
         ldpc_status st = decode_common(h, d_llr + b0 * n_tx * esz, nb, max_iter, stream, &o,
                                        d_bits + b0 * nbytes, d_it + b0, nullptr, nullptr);
