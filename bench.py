@@ -316,8 +316,9 @@ def latency_measure(wl, graph, reps: int = 50):
     int8 with the paper's two strategies (Sec. IV): alpha = 1 thread per row pair (the
     high-throughput kernel) and alpha = 2, 4 cooperating threads per row pair (the
     low-latency kernel, the library's choice for a batch that does not fill the SMs), and
-    the binary16 decoder.  Then small batches (up to two codewords per SM) with alpha 1, 2
-    and 4, which sets where the library switches strategy."""
+    the binary16 decoder, and the cluster split (one codeword on two SMs).  Then small
+    batches (up to two codewords per SM) with alpha 1, 2 and 4 and the cluster split, which
+    sets where the library switches strategy."""
     import torch
 
     import paper_2009_05534_gb300 as ldpc
@@ -340,6 +341,8 @@ def latency_measure(wl, graph, reps: int = 50):
     out = {"int8": lat(q, reps, algo=ldpc.OFFSET)}
     out["int8_by_alpha"] = {str(a): lat(q, reps, algo=ldpc.OFFSET, threads_per_row=a)
                             for a in (1, 2, 4)}
+    # the cluster split: two blocks on two SMs per codeword (alpha 2 in each)
+    out["int8_cluster2"] = lat(q, reps, algo=ldpc.OFFSET, cluster_size=2)
     out["fp16"] = lat(torch.from_numpy(wl.llr_fp16()[:1]).cuda(), reps, algo=ldpc.NORMALISED,
                       alpha=0.75)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
@@ -351,6 +354,7 @@ def latency_measure(wl, graph, reps: int = 50):
         qb = torch.from_numpy(full[:b]).cuda()
         small[str(b)] = {str(a): lat(qb, 10, algo=ldpc.OFFSET, threads_per_row=a)["median_us"]
                          for a in (1, 2, 4)}
+        small[str(b)]["cluster2"] = lat(qb, 10, algo=ldpc.OFFSET, cluster_size=2)["median_us"]
     out["batch_us_by_alpha"] = small
     return {"workload": "one BG1-shaped Z=384 R=1/3 codeword, 10 iterations", **out}
 

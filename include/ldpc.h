@@ -69,7 +69,11 @@ typedef enum {
  *   n_tx         channel LLRs per codeword; 0 = (K_b + n_rows - punct_cols) * Z.
  *   punct_cols   punctured leading columns (default 2, Sec. II).
  *   early_stop   1: stop a codeword when its syndrome is zero after a full iteration.
- *   cluster_size 1 (one thread block per codeword; other values are reserved).
+ *   cluster_size 1: one thread block per codeword.  2: one codeword per cluster of two
+ *                thread blocks on two SMs, each block half of every layer's check rows
+ *                (alpha = 2 threads per row pair), posterior updates exchanged through
+ *                distributed shared memory after every layer; the latency mode for a lone
+ *                codeword; int8 offset min-sum, Z a multiple of 4.  Results are identical.
  *   learned_params device float [max_iter][n_rows][2] = (beta, gamma) for LDPC_LEARNED.
  *   threads_per_row  the paper's alpha (Sec. IV): cooperating threads per check-row pair.
  *                1 = the high-throughput strategy (one thread per row pair, two codewords
@@ -127,8 +131,10 @@ int ldpc_graph_vars(ldpc_graph_t g, int n_rows);
  *   hard_bits_dev  device uint8 [batch][ceil(K/8)] output.
  *   iters_dev      device int32 [batch] output: iterations executed (T without early stop).
  * Host-side argument errors return at once and launch nothing: LDPC_ERR_INVALID_ARG for a
- * threads_per_row other than 0, 1, 2, 4, LDPC_ERR_UNSUPPORTED for 2 or 4 outside the
- * int8 offset decoder or for graphs it cannot hold.  Returns after the launch. */
+ * threads_per_row other than 0, 1, 2, 4 or a cluster_size other than 1, 2;
+ * LDPC_ERR_UNSUPPORTED for threads_per_row 2 or 4 or cluster_size 2 outside the int8 offset
+ * decoder or for graphs they cannot hold (cluster_size 2 takes threads_per_row 0 or 2).
+ * Returns after the launch. */
 ldpc_status ldpc_decode(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,
                         ldpc_stream_t stream, const ldpc_decode_opts *opts,
                         uint8_t *hard_bits_dev, int32_t *iters_dev);

@@ -178,7 +178,7 @@ def _stream_ptr(stream):
 
 def make_opts(llr_type: int, *, algo=None, alpha=0.75, offset=0.0, offset_q=1, n_rows=0,
               n_tx=0, punct_cols=2, early_stop=True, learned=None,
-              threads_per_row=0) -> DecodeOpts:
+              threads_per_row=0, cluster_size=1) -> DecodeOpts:
     o = DecodeOpts()
     lib().ldpc_decode_opts_default(ctypes.byref(o))
     o.llr_type = llr_type
@@ -192,6 +192,7 @@ def make_opts(llr_type: int, *, algo=None, alpha=0.75, offset=0.0, offset_q=1, n
     o.early_stop = int(bool(early_stop))
     o.learned_params = None if learned is None else learned.data_ptr()
     o.threads_per_row = int(threads_per_row)
+    o.cluster_size = int(cluster_size)
     return o
 
 

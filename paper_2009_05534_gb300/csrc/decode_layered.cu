@@ -266,6 +266,12 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    // a cluster of two blocks per codeword when asked for
+    if (p.cluster_size == 2) {
+        if (!cluster_supported(p, llr_type, p.max_deg, (size_t)smem_optin))
+            return LDPC_ERR_UNSUPPORTED;
+        return launch_cluster(p, stream);
+    }
     // the low-latency strategy (alpha cooperating threads per row pair, one codeword per
     // block) when asked for, or by default when the batch does not fill the SMs
     int A = p.threads_per_row;

@@ -202,7 +202,10 @@ static ldpc_status decode_params(ldpc_graph_t h, const void *llr, int batch, int
     }
     if (o.llr_type == LDPC_LLR_INT8 && o.algo != LDPC_OFFSET) return LDPC_ERR_UNSUPPORTED;
     if (o.algo == LDPC_LEARNED && !o.learned_params) return LDPC_ERR_INVALID_ARG;
-    if (o.cluster_size != 1) return LDPC_ERR_UNSUPPORTED;
+    if (o.cluster_size != 1 && o.cluster_size != 2) return LDPC_ERR_INVALID_ARG;
+    if (o.cluster_size == 2 &&
+        (o.llr_type != LDPC_LLR_INT8 || flooding || (o.threads_per_row != 0 && o.threads_per_row != 2)))
+        return LDPC_ERR_UNSUPPORTED;
     if (o.threads_per_row != 0 && o.threads_per_row != 1 && o.threads_per_row != 2 &&
         o.threads_per_row != 4)
         return LDPC_ERR_INVALID_ARG;
@@ -256,6 +259,7 @@ static ldpc_status decode_params(ldpc_graph_t h, const void *llr, int batch, int
     p.in_rows = nullptr;
     p.out_rows = nullptr;
     p.threads_per_row = o.threads_per_row;
+    p.cluster_size = o.cluster_size;
     p.queue = nullptr;
     *o_out = o;
     return LDPC_OK;

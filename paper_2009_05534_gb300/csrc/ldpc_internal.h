@@ -71,6 +71,7 @@ struct DecodeParams {
     const int32_t *in_rows;   // [batch] LLR row of codeword b, or null (row b)
     const int32_t *out_rows;  // [batch] output row of codeword b, or null (row b)
     int threads_per_row;      // cooperating threads per row pair (0 = automatic)
+    int cluster_size;         // 1, or 2: one codeword per cluster of two blocks
     int *queue;               // device [2] work counters of the launch's stream, or null
 };
 
@@ -101,6 +102,11 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
 // Tensor Memory, per-lane stopping and refill (decode_tmem_pair.cu).
 bool pair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_pair(const DecodeParams &p, cudaStream_t stream);
+
+// One codeword per cluster of two blocks on two SMs, each block half of the row pairs,
+// posterior updates exchanged through distributed shared memory (decode_cluster.cu).
+bool cluster_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
+ldpc_status launch_cluster(const DecodeParams &p, cudaStream_t stream);
 
 // One-codeword kernel with A = 2 or 4 cooperating threads per row pair, messages in
 // Tensor Memory (decode_tmem_ll.cu): the low-latency strategy.

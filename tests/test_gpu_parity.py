@@ -371,6 +371,70 @@ def test_batch_kernel_more_streams_than_counters(ldpc):
     g.close()
 
 
+# ------------------------------------------- cluster split (one codeword on two SMs)
+
+@pytest.mark.parametrize("T", [1, 10])
+def test_cluster_split_bit_exact(ldpc, T):
+    """cluster_size 2: each codeword decoded by a pair of blocks that exchange posterior
+    updates through distributed shared memory after every layer; every posterior, message,
+    hard bit and iteration count equals the oracle's."""
+    wl, q, ref = _ref_bg1(T)
+    bits, iters, post, c2v = _gpu(ldpc, wl, q, T, early_stop=False, cluster_size=2)
+    assert np.array_equal(post, ref.post)
+    assert np.array_equal(c2v, ref.c2v)
+    assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
+    assert (iters == T).all()
+
+
+def test_cluster_split_early_stop_several_codewords(ldpc):
+    """More codewords than clusters (each cluster decodes several in turn) with the stopping
+    rule combined across the pair: iteration counts and bits match the oracle."""
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    B = n_sm + 9
+    wl = make_workload("BG1", 384, B, 1.5, seed=37)
+    q = wl.llr_int8()
+    ref = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=10, early_stop=True, threads=8)
+    assert len(np.unique(ref.iters)) >= 3
+    bits, iters = _gpu(ldpc, wl, q, 10, early_stop=True, debug=False, cluster_size=2)
+    assert np.array_equal(iters, ref.iters)
+    assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
+
+
+@pytest.mark.parametrize("kind,Z,rate", [("BG2", 4, None), ("BG1", 100, "2/3"),
+                                         ("BG2", 256, "1/3")])
+def test_cluster_split_other_shapes(ldpc, kind, Z, rate):
+    """Small Z (one warp per block, spare threads) and other rates."""
+    wl = make_workload(kind, Z, 5, 2.0, rate=None if rate is None else Fraction(rate), seed=Z)
+    q = wl.llr_int8()
+    ref = oracle.decode_layered(wl.base, wl.K_b, Z, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=6, early_stop=True, want_post=True, want_c2v=True)
+    bits, iters, post, c2v = _gpu(ldpc, wl, q, 6, early_stop=True, n_rows=wl.n_rows,
+                                  n_tx=wl.n_tx, cluster_size=2)
+    assert np.array_equal(iters, ref.iters)
+    assert np.array_equal(post, ref.post)
+    assert np.array_equal(c2v, ref.c2v)
+    assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
+
+
+def test_cluster_split_rejections(ldpc):
+    wl = make_workload("BG2", 16, 2, 3.0, seed=1)
+    g = ldpc.Graph(wl.base, wl.K_b, 16)
+    q = torch.from_numpy(wl.llr_int8()).cuda()
+    with pytest.raises(ldpc.LdpcError):
+        ldpc.decode(g, q, 5, cluster_size=3)               # 1 or 2
+    with pytest.raises(ldpc.LdpcError):
+        ldpc.decode(g, q.float(), 5, cluster_size=2)       # int8 only
+    with pytest.raises(ldpc.LdpcError):
+        ldpc.decode(g, q, 5, cluster_size=2, threads_per_row=4)
+    g.close()
+    wl = make_workload("BG2", 18, 2, 3.0, seed=1)          # Z not a multiple of 4
+    g = ldpc.Graph(wl.base, wl.K_b, 18)
+    with pytest.raises(ldpc.LdpcError):
+        ldpc.decode(g, torch.from_numpy(wl.llr_int8()).cuda(), 5, cluster_size=2)
+    g.close()
+
+
 # ------------------------------------------------- low-latency strategy (alpha threads)
 
 def test_low_latency_batch_beyond_sm_count(ldpc):
