@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-slots", type=int, default=2000,
+    ap.add_argument("--serve-slots", type=int, default=10000,
                     help="slots of the mixed-traffic serving measurement (0 = skip)")
     ap.add_argument("--no-high-load", dest="high_load", action="store_false",
                     help="skip the rate-8/9 QAM int8-vs-binary16 measurement")
