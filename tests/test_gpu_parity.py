@@ -417,6 +417,32 @@ def test_cluster_split_other_shapes(ldpc, kind, Z, rate):
     assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
 
 
+def test_cluster_split_row_maps_and_host_buffers(ldpc):
+    """The cluster split through decode_rows (scattered pool rows in and out) and through the
+    host-buffer entry point equals the oracle."""
+    wl = make_workload("BG1", 96, 20, 1.75, seed=44)
+    q = wl.llr_int8()
+    g = ldpc.Graph(wl.base, wl.K_b, 96)
+    perm = np.random.default_rng(4).permutation(20)
+    in_rows = torch.tensor(perm[:12], dtype=torch.int32).cuda()
+    out_rows = torch.tensor(perm[8:20], dtype=torch.int32).cuda()
+    nb = (wl.K + 7) // 8
+    bits = torch.zeros((20, nb), dtype=torch.uint8, device="cuda")
+    iters = torch.full((20,), -1, dtype=torch.int32, device="cuda")
+    ldpc.decode_rows(g, torch.from_numpy(q).cuda(), in_rows, out_rows, 6, bits=bits,
+                     iters=iters, early_stop=True, cluster_size=2)
+    torch.cuda.synchronize()
+    ref = oracle.decode_layered(wl.base, wl.K_b, 96, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=6, early_stop=True)
+    assert np.array_equal(ldpc.unpack_bits(bits.cpu().numpy()[perm[8:20]], wl.K),
+                          ref.bits[perm[:12]])
+    assert np.array_equal(iters.cpu().numpy()[perm[8:20]], ref.iters[perm[:12]])
+    hb, hi = ldpc.decode_host(g, torch.from_numpy(q), 6, early_stop=True, cluster_size=2)
+    assert np.array_equal(ldpc.unpack_bits(hb.numpy(), wl.K), ref.bits)
+    assert np.array_equal(hi.numpy(), ref.iters)
+    g.close()
+
+
 def test_cluster_split_rejections(ldpc):
     wl = make_workload("BG2", 16, 2, 3.0, seed=1)
     g = ldpc.Graph(wl.base, wl.K_b, 16)
