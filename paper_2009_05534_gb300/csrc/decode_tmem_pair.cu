@@ -212,15 +212,25 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
     uint32_t pending = 0u;               // bit S: a copy into buffer S issued, not consumed
     bool failed = false;
     // thread 0 claims the next codeword and starts its copy into buffer S (free: no thread
-    // reads it); every thread gets the codeword, or -1 once the batch is exhausted
-    auto claim = [&](int S) -> int {
+    // reads it); every thread gets the codeword, or -1 once the batch is exhausted.  A claim
+    // to stage ahead (ahead = true) is skipped near the end of the batch: blocks refill at
+    // about the same time (always, at a fixed iteration count), and a block that staged one
+    // of the last codewords would take it from a block whose lane is still empty (a batch
+    // of k full rounds took k + 1 rounds).
+    int k_last = 0;                      // thread 0: the index of its last claim
+    auto claim = [&](int S, bool ahead) -> int {
         if (drained) return -1;
         const int slot = n_claims & 1;   // two slots: one barrier per claim suffices
-        ++n_claims;
         if (tid == 0) {
-            const int k = p.queue ? atomicAdd(p.queue, 1)
-                                  : (int)blockIdx.x + (n_claims - 1) * (int)gridDim.x;
-            const int c = k < p.batch ? k : -1;
+            int c = -2;                  // -2: not staged (lanes claim on demand)
+            // what remains is at most batch - k_last; other blocks may have claimed up to
+            // a round of lanes since, hence the margin of twice the lanes
+            if (!ahead || !p.queue || p.batch - k_last > 4 * (int)gridDim.x) {
+                const int k = p.queue ? atomicAdd(p.queue, 1)
+                                      : (int)blockIdx.x + n_claims * (int)gridDim.x;
+                k_last = k;
+                c = k < p.batch ? k : -1;
+            }
             s_claim[slot] = c;
             if (c >= 0 && pp.use_tma)
                 bulk_load(stage + S * pp.stage_bytes, llr_all + in_row(p, c) * p.n_tx,
@@ -228,11 +238,12 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
         }
         named_sync(1, nthr);
         const int c = s_claim[slot];
-        if (c < 0)
+        if (c != -2) ++n_claims;
+        if (c == -1)
             drained = true;
-        else if (pp.use_tma)
+        else if (c >= 0 && pp.use_tma)
             pending |= 1u << S;
-        return c;
+        return c < 0 ? -1 : c;
     };
     // a0 for lane X: its messages to zero (byte 0x80), its posteriors from the channel
     // LLRs; false (for every thread) if the staged copy timed out
@@ -305,15 +316,15 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
         }
     };
 
-    cw[0] = claim(0);
-    cw[1] = claim(1);
+    cw[0] = claim(0, false);
+    cw[1] = claim(1, false);
 #pragma unroll
     for (int X = 0; X < 2 && !failed; ++X)
         if (cw[X] >= 0) failed = !init_lane(X);
     named_sync(1, nthr);                             // buffer 0 free again
     if (!failed) {
         sbuf = 0;
-        staged = claim(sbuf);
+        staged = claim(sbuf, true);
     }
 
     int ib = 0;                                      // iterations run by the block
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
                 staged = -1;
             } else {
                 b = lastb ^ 1;                       // the other buffer may still be read
-                cw[X] = claim(b);
+                cw[X] = claim(b, false);
             }
             lastb = b;
             buf[X] = b;
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
         named_sync(1, nthr);                         // refilled posteriors visible; staging free
         if (!failed && staged < 0) {
             sbuf = lastb ^ 1;
-            staged = claim(sbuf);
+            staged = claim(sbuf, true);
         }
     }
     // a copy still in flight after a timeout must not outlive the block (bounded waits)
