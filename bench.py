@@ -11,6 +11,14 @@ the hot path: load, gather, v->c, check node, write-back, output).
 Metric: decoded information Gbit/s = batch * K / time, timed with CUDA events on the
 decode stream; inputs rotate over device copies totalling more than twice the L2 size, so
 no step reads its LLRs from L2.  `--impl reference` times the CPU oracle instead.
+
+Beside the headline the JSON line carries: the ALU roofline fraction and the profiled DRAM
+traffic of the decode kernel; the early-stop figure; an end-to-end figure through the
+host-buffer C-ABI call; a whole-rounds batch (8 codewords per SM) for context; and, on rank
+0, the slot-serving leg (10 000 slots of mixed traffic, p50/p99 latency), the latency leg
+(a lone codeword with each strategy, the cluster split, small batches), the BLER curve,
+the flooding comparison, the rate-8/9 high-load leg (int8 and binary16) and the learned
+tables against plain min-sum at equal BLER.  --no-<leg> flags skip them.
 """
 from __future__ import annotations
 

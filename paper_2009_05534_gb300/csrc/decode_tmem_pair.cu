@@ -21,9 +21,10 @@
 // The two codewords of a block advance in lockstep through the layers, but each lane keeps
 // its own codeword and iteration count: after every full iteration each lane applies the
 // stopping rule (or the iteration cap) on its own, writes its outputs when it stops, and is
-// refilled at once with the block's next codeword (LLRs already staged by a 1-D bulk copy),
-// which then starts its first iteration at layer 0 while the other lane carries on.  A lane
-// with no codeword left runs along without writing anything.
+// refilled at once with the block's next codeword (its LLRs staged ahead by a 1-D bulk copy,
+// or, near the end of the batch, claimed and copied then), which starts its first
+// iteration at layer 0 while the other lane carries on.  A lane with no codeword left runs
+// along without writing anything.
 //
 // Arithmetic (exact on these integers, so bit-identical to 8-bit fixed point): posteriors
 // as binary16 L + 1279 in shared memory (on [1152, 1406] binary16 has spacing 1; word
