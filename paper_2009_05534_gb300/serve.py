@@ -30,6 +30,7 @@ with a fake backend.
 """
 from __future__ import annotations
 
+import gc
 import time
 from dataclasses import dataclass
 
@@ -260,13 +261,24 @@ class GpuBackend:
 
 
 def run_paced(scheduler: SlotScheduler, counts, slot_us: float = 500.0) -> float:
-    """counts[s] arrivals at slot s, slots paced in real time; returns the wall time."""
-    t0 = time.perf_counter()
-    for s, n in enumerate(counts):
-        target = t0 + s * slot_us * 1e-6
-        while time.perf_counter() < target:
-            pass
-        scheduler.submit(int(n))
-        scheduler.step()
-    scheduler.drain()
-    return time.perf_counter() - t0
+    """counts[s] arrivals at slot s, slots paced in real time; returns the wall time.
+
+    The interpreter's cyclic garbage collector is paused for the duration (a collection
+    over the loop's many short-lived arrays can stall a slot by milliseconds) and run once
+    afterwards."""
+    was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for s, n in enumerate(counts):
+            target = t0 + s * slot_us * 1e-6
+            while time.perf_counter() < target:
+                pass
+            scheduler.submit(int(n))
+            scheduler.step()
+        scheduler.drain()
+        return time.perf_counter() - t0
+    finally:
+        if was_enabled:
+            gc.enable()
+        gc.collect()
