@@ -151,6 +151,23 @@ ldpc_status ldpc_decode_rows(ldpc_graph_t g, const void *llr_dev, const int32_t 
                              ldpc_stream_t stream, const ldpc_decode_opts *opts,
                              uint8_t *hard_bits_dev, int32_t *iters_dev);
 
+/* As ldpc_decode_rows with the row maps in host memory (serving support): the library
+ * copies them into a pinned staging buffer and uploads them on `stream` ahead of the
+ * launch, so a slot's row-mapped batch is one call with no separate upload by the caller.
+ *   in_rows_host, out_rows_host  host int32 [batch], read before the call returns (the
+ *                                caller may reuse them at once); a negative row is
+ *                                LDPC_ERR_INVALID_ARG.  Rows must lie inside the caller's
+ *                                buffers and out rows must be distinct.
+ * The staging buffers belong to the library, one pair per (device, stream), grown on demand
+ * (LDPC_ERR_OUT_OF_MEMORY if that fails) and kept for the process's lifetime; a call waits
+ * on the host for the previous upload on the same stream to finish before refilling them.
+ * Everything else as for ldpc_decode. */
+ldpc_status ldpc_decode_rows_host_maps(ldpc_graph_t g, const void *llr_dev,
+                                       const int32_t *in_rows_host,
+                                       const int32_t *out_rows_host, int batch, int max_iter,
+                                       ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                                       uint8_t *hard_bits_dev, int32_t *iters_dev);
+
 /* As ldpc_decode, and also writes the final posteriors and check-to-variable messages
  * (for parity tests):
  *   post_dev  device [batch][(K_b + n_rows) * Z] in the LLR type.

@@ -55,7 +55,7 @@ ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_dest
                "ldpc_learned_workspace_floats", "ldpc_learned_forward", "ldpc_learned_backward",
                "ldpc_learned_forward_iter", "ldpc_learned_backward_iter",
                "ldpc_flooding_workspace_floats", "ldpc_decode_flooding", "ldpc_decode_rows",
-               "ldpc_selftest_wait_timeout")
+               "ldpc_decode_rows_host_maps", "ldpc_selftest_wait_timeout")
 
 
 def lib():
@@ -88,6 +88,10 @@ def lib():
             L.ldpc_decode_list.argtypes = [ctypes.POINTER(WorkItem), i, P,
                                            ctypes.POINTER(DecodeOpts)]
             L.ldpc_decode_list.restype = i
+            # the same entry point taking the item table as a plain address (raw words)
+            L.decode_list_words = L["ldpc_decode_list"]
+            L.decode_list_words.argtypes = [P, i, P, ctypes.POINTER(DecodeOpts)]
+            L.decode_list_words.restype = i
             L.ldpc_decode_list_noalloc.argtypes = [ctypes.POINTER(WorkItem), i, P,
                                                    ctypes.POINTER(DecodeOpts)]
             L.ldpc_decode_list_noalloc.restype = i
@@ -100,6 +104,8 @@ def lib():
             L.ldpc_decode_rows.argtypes = [P, P, P, P, i, i, P, ctypes.POINTER(DecodeOpts),
                                            P, P]
             L.ldpc_decode_rows.restype = i
+            L.ldpc_decode_rows_host_maps.argtypes = L.ldpc_decode_rows.argtypes
+            L.ldpc_decode_rows_host_maps.restype = i
             L.ldpc_selftest_wait_timeout.argtypes = [ctypes.c_uint, P,
                                                      ctypes.POINTER(ctypes.c_ulonglong)]
             L.ldpc_selftest_wait_timeout.restype = i
@@ -170,8 +176,11 @@ class Graph:
 
 
 def _stream_ptr(stream):
-    import torch
+    """A torch stream (None: the current one) or a raw stream handle as ctypes.c_void_p."""
+    if isinstance(stream, ctypes.c_void_p):
+        return stream
     if stream is None:
+        import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
 
@@ -280,6 +289,30 @@ def decode_rows(graph: Graph, llr, in_rows, out_rows, max_iter: int, *, bits, it
     return bits, iters
 
 
+def decode_rows_host_maps(graph: Graph, llr, in_rows, out_rows, max_iter: int, *, bits, iters,
+                          stream=None, opts: DecodeOpts | None = None, **kw):
+    """decode_rows with the row maps given in host memory (int32 numpy arrays of the batch
+    length; ldpc_decode_rows_host_maps stages and uploads them on the stream).  opts: a
+    DecodeOpts from make_opts, reused across calls instead of building one from kw."""
+    i = np.ascontiguousarray(in_rows, dtype=np.int32)
+    o_ = np.ascontiguousarray(out_rows, dtype=np.int32)
+    if i.shape != o_.shape or i.ndim != 1:
+        raise ValueError("row maps must be 1-D and of one length")
+    if opts is None:
+        if not llr.is_cuda:
+            raise ValueError("llr must be a CUDA tensor")
+        kw.setdefault("n_tx", llr.shape[1])
+        opts = make_opts(_llr_type(llr), **kw)
+    _check(lib().ldpc_decode_rows_host_maps(graph.handle, ctypes.c_void_p(llr.data_ptr()),
+                                            i.ctypes.data, o_.ctypes.data, len(i),
+                                            int(max_iter), _stream_ptr(stream),
+                                            ctypes.byref(opts),
+                                            ctypes.c_void_p(bits.data_ptr()),
+                                            ctypes.c_void_p(iters.data_ptr())),
+           "ldpc_decode_rows_host_maps")
+    return bits, iters
+
+
 def decode_flooding(graph: Graph, llr, max_iter: int, *, want_post: bool = False,
                     stream=None, workspace=None, **kw):
     """Flooding-schedule decode of fp32 llr [batch][n_tx] (CUDA): min-sum (algo NORMALISED /
@@ -345,12 +378,33 @@ work_item_dtype = np.dtype({
     "itemsize": ctypes.sizeof(WorkItem)})
 
 
-def decode_list_array(items: np.ndarray, *, stream=None, early_stop=True):
-    """ldpc_decode_list on a numpy record array of ``work_item_dtype`` (asynchronous)."""
+def decode_list_array(items: np.ndarray, *, stream=None, early_stop=True,
+                      opts: DecodeOpts | None = None):
+    """ldpc_decode_list on a numpy record array of ``work_item_dtype`` (asynchronous).
+    opts: a DecodeOpts from make_opts(LLR_INT8, ...) reused across calls (early_stop is then
+    taken from it)."""
     arr = np.ascontiguousarray(items, dtype=work_item_dtype)
-    o = make_opts(LLR_INT8, early_stop=early_stop)
+    o = make_opts(LLR_INT8, early_stop=early_stop) if opts is None else opts
     _check(lib().ldpc_decode_list(arr.ctypes.data_as(ctypes.POINTER(WorkItem)), len(arr),
                                   _stream_ptr(stream), ctypes.byref(o)), "ldpc_decode_list")
+
+
+WORK_ITEM_WORDS = ctypes.sizeof(WorkItem) // 8
+
+
+def decode_list_words(words: np.ndarray, *, stream=None, early_stop=True,
+                      opts: DecodeOpts | None = None):
+    """ldpc_decode_list on work items held as raw 64-bit words: a C-contiguous uint64 array
+    [n][WORK_ITEM_WORDS] laid out byte for byte as ``ldpc_work_item`` (e.g.
+    ``items.view(np.uint64).reshape(n, -1)`` of a ``work_item_dtype`` array).  Gathering
+    and patching rows of such an array is much cheaper than on a record array, which
+    matters on a per-slot serving path."""
+    if (words.dtype != np.uint64 or words.ndim != 2 or words.shape[1] != WORK_ITEM_WORDS
+            or not words.flags.c_contiguous):
+        raise ValueError("work items must be a C-contiguous uint64 [n][WORK_ITEM_WORDS] array")
+    o = make_opts(LLR_INT8, early_stop=early_stop) if opts is None else opts
+    _check(lib().decode_list_words(words.ctypes.data, words.shape[0], _stream_ptr(stream),
+                                   ctypes.byref(o)), "ldpc_decode_list")
 
 
 def decode_list(items, *, stream=None, early_stop=True):

@@ -464,8 +464,7 @@ ldpc_status launch_cluster(const DecodeParams &p, cudaStream_t stream) {
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (set_dyn_smem(reinterpret_cast<const void *>(cluster_kernel), smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     int n_cl = n_sm / 2;
     if (n_cl > p.batch) n_cl = p.batch;

@@ -207,12 +207,11 @@ ldpc_status launch_flooding(const DecodeParams &p, float *ws, cudaStream_t strea
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = flood_smem(p);
     if (smem > (size_t)optin) return LDPC_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(flood_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (set_dyn_smem(reinterpret_cast<const void *>(flood_kernel), smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     const int threads = 256;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flood_kernel, threads, smem) !=
+    if (blocks_per_sm(&per_sm, reinterpret_cast<const void *>(flood_kernel), threads, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;

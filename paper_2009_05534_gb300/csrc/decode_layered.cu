@@ -241,14 +241,13 @@ ldpc_status launch_t(const DecodeParams &p, cudaStream_t stream) {
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (smem > (size_t)smem_optin) return LDPC_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(layered_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (set_dyn_smem(reinterpret_cast<const void *>(layered_kernel<Ar>), smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     int threads = ((p.Z + 31) / 32) * 32;
     if (threads > 1024) threads = 1024;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, layered_kernel<Ar>, threads,
-                                                      smem) != cudaSuccess ||
+    if (blocks_per_sm(&per_sm, reinterpret_cast<const void *>(layered_kernel<Ar>), threads,
+                      smem) != cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;
     int grid = n_sm * per_sm;

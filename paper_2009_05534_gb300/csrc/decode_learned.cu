@@ -329,13 +329,13 @@ ldpc_status launch_learned(const DecodeParams &dp, int T, const float *params, c
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)optin) return LDPC_ERR_UNSUPPORTED;
     auto kern = backward ? learned_bwd_kernel : learned_fwd_kernel;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (set_dyn_smem(reinterpret_cast<const void *>(kern), smem) !=
         cudaSuccess)
         return LDPC_ERR_CUDA;
     int threads = ((dp.Z + 31) / 32) * 32;
     if (threads > 512) threads = 512;      // rows beyond the block loop
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
+    if (blocks_per_sm(&per_sm, reinterpret_cast<const void *>(kern), threads, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;

@@ -352,12 +352,11 @@ ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stre
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(rowpair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (set_dyn_smem(reinterpret_cast<const void *>(rowpair_kernel), smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     const int threads = ((H + 31) / 32) * 32;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rowpair_kernel, threads, smem) !=
+    if (blocks_per_sm(&per_sm, reinterpret_cast<const void *>(rowpair_kernel), threads, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;
@@ -376,11 +375,10 @@ ldpc_status launch_list(const ListItem *d_items, int n_items, int *d_counter, si
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)optin) return LDPC_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (set_dyn_smem(reinterpret_cast<const void *>(list_kernel), smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, list_kernel, kThreadsP, smem) !=
+    if (blocks_per_sm(&per_sm, reinterpret_cast<const void *>(list_kernel), kThreadsP, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;

@@ -502,12 +502,12 @@ ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream) {
     size_t smem = l.total;
     const size_t floor_b = (size_t)smem_sm / (by_tmem + 1) + 1024;
     if (smem < floor_b && floor_b <= (size_t)smem_optin) smem = floor_b;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (set_dyn_smem(reinterpret_cast<const void *>(kern), smem) !=
         cudaSuccess)
         return LDPC_ERR_CUDA;
     const int threads = sh.cw * sh.wpc * 32;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
+    if (blocks_per_sm(&per_sm, reinterpret_cast<const void *>(kern), threads, smem) !=
             cudaSuccess ||
         per_sm < 1)
         return LDPC_ERR_UNSUPPORTED;

@@ -403,12 +403,10 @@ ldpc_status launch_tmem_ll(const DecodeParams &p, int A, cudaStream_t stream) {
     int grid = p.batch < n_sm ? p.batch : n_sm;
     cudaError_t err;
     if (A == 2) {
-        err = cudaFuncSetAttribute(tmem_ll_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
+        err = set_dyn_smem(reinterpret_cast<const void *>(tmem_ll_kernel<2>), smem);
         if (err == cudaSuccess) tmem_ll_kernel<2><<<grid, threads, smem, stream>>>(pp);
     } else {
-        err = cudaFuncSetAttribute(tmem_ll_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
+        err = set_dyn_smem(reinterpret_cast<const void *>(tmem_ll_kernel<4>), smem);
         if (err == cudaSuccess) tmem_ll_kernel<4><<<grid, threads, smem, stream>>>(pp);
     }
     if (err != cudaSuccess) return LDPC_ERR_CUDA;

@@ -469,8 +469,7 @@ ldpc_status launch_pair(const DecodeParams &p, cudaStream_t stream) {
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (set_dyn_smem(reinterpret_cast<const void *>(pair_kernel), smem) != cudaSuccess)
         return LDPC_ERR_CUDA;
     const int threads = ((p.Z + 31) / 32) * 32;
     int grid = (p.batch + 1) / 2;

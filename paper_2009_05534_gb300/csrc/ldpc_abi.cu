@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -18,6 +19,42 @@ namespace ldpc {
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static std::mutex g_attr_mu;
+static std::map<std::pair<const void *, int>, size_t> g_dyn_smem;
+static std::map<std::tuple<const void *, int, int, size_t>, int> g_occupancy;
+
+cudaError_t set_dyn_smem(const void *kernel, size_t smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const auto key = std::make_pair(kernel, dev);
+    const auto it = g_dyn_smem.find(key);
+    if (it != g_dyn_smem.end() && it->second == smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        g_dyn_smem[key] = smem;
+    else
+        g_dyn_smem.erase(key);
+    return e;
+}
+
+cudaError_t blocks_per_sm(int *per_sm, const void *kernel, int threads, size_t smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const auto key = std::make_tuple(kernel, dev, threads, smem);
+    const auto it = g_occupancy.find(key);
+    if (it != g_occupancy.end()) {
+        *per_sm = it->second;
+        return cudaSuccess;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, threads, smem);
+    if (e == cudaSuccess) g_occupancy[key] = *per_sm;
+    return e;
+}
+
 // Per-(device, stream) workspace of the work-list decode: device work table + counter, and
 // a pinned host staging copy of the table guarded by an event.
 struct ListWorkspace {
@@ -26,6 +63,11 @@ struct ListWorkspace {
     ListItem *h_items = nullptr;
     size_t cap = 0;
     cudaEvent_t copied = nullptr;
+    // row maps of ldpc_decode_rows_host_maps: [in rows | out rows], pinned and device
+    int32_t *d_maps = nullptr;
+    int32_t *h_maps = nullptr;
+    size_t map_cap = 0;             // codewords
+    cudaEvent_t maps_copied = nullptr;
 };
 static std::mutex g_ws_mu;
 static std::map<std::pair<int, cudaStream_t>, ListWorkspace> g_ws;
@@ -300,6 +342,63 @@ ldpc_status ldpc_decode_rows(ldpc_graph_t g, const void *llr_dev, const int32_t 
     p.out_rows = out_rows_dev;
     p.queue = ldpc::graph_queue(reinterpret_cast<Graph *>(g), reinterpret_cast<cudaStream_t>(stream));
     return ldpc::launch_layered(p, o.llr_type, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ldpc_status ldpc_decode_rows_host_maps(ldpc_graph_t g, const void *llr_dev,
+                                       const int32_t *in_rows_host,
+                                       const int32_t *out_rows_host, int batch, int max_iter,
+                                       ldpc_stream_t stream, const ldpc_decode_opts *opts,
+                                       uint8_t *hard_bits_dev, int32_t *iters_dev) {
+    ldpc::DecodeParams p;
+    ldpc_decode_opts o;
+    bool empty = false;
+    const ldpc_status st = decode_params(g, llr_dev, batch, max_iter, opts, hard_bits_dev,
+                                         iters_dev, nullptr, nullptr, false, &p, &o, &empty);
+    if (st != LDPC_OK || empty) return st;
+    if (!in_rows_host || !out_rows_host) return LDPC_ERR_INVALID_ARG;
+    for (int b = 0; b < batch; ++b)
+        if (in_rows_host[b] < 0 || out_rows_host[b] < 0) return LDPC_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(ldpc::g_ws_mu);
+    ldpc::ListWorkspace &ws = ldpc::g_ws[std::make_pair(dev, s)];
+    if (ws.map_cap < (size_t)batch) {
+        if (ws.maps_copied) cudaEventSynchronize(ws.maps_copied);
+        cudaFree(ws.d_maps);
+        cudaFreeHost(ws.h_maps);
+        ws.d_maps = nullptr;
+        ws.h_maps = nullptr;
+        ws.map_cap = 0;
+        size_t cap = 256;
+        while (cap < (size_t)batch) cap *= 2;
+        if (cudaMalloc(&ws.d_maps, 2 * cap * sizeof(int32_t)) != cudaSuccess ||
+            cudaMallocHost(&ws.h_maps, 2 * cap * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(ws.d_maps);
+            cudaFreeHost(ws.h_maps);
+            ws.d_maps = nullptr;
+            ws.h_maps = nullptr;
+            return LDPC_ERR_OUT_OF_MEMORY;
+        }
+        ws.map_cap = cap;
+    }
+    if (!ws.maps_copied &&
+        cudaEventCreateWithFlags(&ws.maps_copied, cudaEventDisableTiming) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    // the pinned staging copy may still feed the previous call's upload; the device copy is
+    // ordered after the previous launch on this stream
+    if (cudaEventSynchronize(ws.maps_copied) != cudaSuccess) return LDPC_ERR_CUDA;
+    std::memcpy(ws.h_maps, in_rows_host, (size_t)batch * sizeof(int32_t));
+    std::memcpy(ws.h_maps + batch, out_rows_host, (size_t)batch * sizeof(int32_t));
+    if (cudaMemcpyAsync(ws.d_maps, ws.h_maps, 2 * (size_t)batch * sizeof(int32_t),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(ws.maps_copied, s) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    p.in_rows = ws.d_maps;
+    p.out_rows = ws.d_maps + batch;
+    p.queue = ldpc::graph_queue(reinterpret_cast<Graph *>(g), s);
+    return ldpc::launch_layered(p, o.llr_type, s);
 }
 
 ldpc_status ldpc_decode_debug(ldpc_graph_t g, const void *llr_dev, int batch, int max_iter,

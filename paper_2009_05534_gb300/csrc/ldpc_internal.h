@@ -152,4 +152,11 @@ ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t sme
 
 void count_launch();
 
+// Launch set-up kept off the per-call path: a kernel's dynamic shared-memory limit is set
+// only when a launch asks for a different amount than the last one on this device, and
+// occupancy answers are remembered per (kernel, device, threads, dynamic shared memory).
+// Both return what the CUDA runtime call they stand for would have returned.
+cudaError_t set_dyn_smem(const void *kernel, size_t smem);
+cudaError_t blocks_per_sm(int *per_sm, const void *kernel, int threads, size_t smem);
+
 }  // namespace ldpc

@@ -5,22 +5,25 @@ slot of 250 us to 1 ms; Sec. V: the 500 us target at 10 iterations).  This modul
 serving loop around the decoder: transport blocks of mixed base graph, lifting size and
 rate arrive continuously; at every slot boundary the server
 
-1. retires the slot batches whose completion event has fired (their output buffers return
-   to the arena and their latencies are recorded),
-2. admits waiting blocks first-come first-served while the output arena has room
+1. admits waiting blocks first-come first-served while the output arena has room
    (admission by memory: a block that does not fit waits for a later slot),
-3. decodes everything admitted in that slot with one work-list launch (`ldpc_decode_list`)
+2. decodes everything admitted in that slot with one work-list launch (`ldpc_decode_list`)
    on the next stream of a small round-robin pool, so new slots start while earlier ones
    are still running on the device; blocks for the learned decoder (one graph and
-   (beta, gamma) table, binary16 LLRs) go to one row-mapped launch (`ldpc_decode_rows`) on
-   a stream of their own, and the slot completes when both have.
+   (beta, gamma) table, binary16 LLRs) go to one row-mapped launch
+   (`ldpc_decode_rows_host_maps`, which uploads the slot's row maps itself) on a stream of
+   their own, and the slot completes when both have,
+3. retires the slot batches whose completion event has fired (their output buffers return
+   to the arena and their latencies are recorded); when the arena cannot take every
+   waiting block this happens before admission instead.
 
 Graphs live on the device for the server's lifetime.  Channel LLRs are read from device
 memory (the demapper's output buffers); the decoder's messages and posteriors never leave
 the SM.  Latency of a block = (slots it waited for admission) x slot length + device time
 from the start of its admission slot to the completion of its slot batch (CUDA events; the
-start event is recorded on an idle stream so it marks the slot boundary even while the
-decode streams are busy).
+start event is recorded on an idle stream as the slot's first action, so it marks the slot
+boundary even while the decode streams are busy and the host's retirement, admission and
+launch work counts towards the latency).
 
 Host cost per slot is kept independent of Python object churn: requests are integer ids
 assigned in arrival order (so FIFO admission is a contiguous id range), their attributes
@@ -54,6 +57,7 @@ class SlotScheduler:
       done(handle) -> bool                            non-blocking completion test
       wait(handle) -> None                            blocking wait
       finish(handle, ids, outs) -> device_us          per-batch device latency, results kept
+    and may provide slot_start() -> None, called first thing at every slot boundary.
     """
 
     def __init__(self, backend, slot_us: float = 500.0, max_requests: int = 1 << 22):
@@ -93,8 +97,18 @@ class SlotScheduler:
         self.in_flight = keep
 
     def step(self) -> np.ndarray:
-        """One slot boundary: retire finished batches, admit, launch.  Returns admitted ids."""
-        self._retire()
+        """One slot boundary: admit, launch, retire finished batches.  Returns admitted ids.
+
+        A backend with a ``slot_start()`` method is told of the boundary first, so that its
+        latency clock also covers the host work before the launch.  Finished batches are
+        retired before admission only when the free buffers do not cover every waiting
+        request (only then can retiring change what is admitted); otherwise after the
+        launch, off the path to the device."""
+        mark = getattr(self.backend, "slot_start", None)
+        if mark is not None:
+            mark()
+        if self.n_waiting > len(self.free):
+            self._retire()
         k = min(self.n_waiting, len(self.free))
         ids = np.arange(self.head, self.head + k)
         if k:
@@ -104,6 +118,7 @@ class SlotScheduler:
             self.admit[ids] = self.slot
             self.in_flight.append(_Batch(self.slot, ids, outs,
                                          self.backend.launch(self.slot, ids, outs)))
+        self._retire()
         self.slot += 1
         return ids
 
@@ -149,52 +164,100 @@ class GpuBackend:
     LLR pointer, n_rows, n_tx and max_iter filled in; the output pointers are set at
     admission from the arena.  ks: information bits per request id.  learned: optional
     LearnedClass; its requests of a slot are decoded by one row-mapped learned decode
-    (`ldpc_decode_rows`) on the same stream, into an arena of their own.
+    (`ldpc_decode_rows_host_maps`, row maps from host memory) on a stream of its own, into
+    an arena of their own.
+
+    Host work per slot is part of every block's latency (the slot's start event is recorded
+    before it), so the per-slot path reuses what does not change: the decode options, the
+    raw stream handles and a pool of timing events.
     """
 
     def __init__(self, table: np.ndarray, ks: np.ndarray, n_buffers: int, kmax: int,
                  n_streams: int = 4, early_stop: bool = True, keep_results: bool = False,
                  learned: LearnedClass | None = None):
+        import ctypes
+
         import torch
 
         import paper_2009_05534_gb300 as ldpc
         self.torch, self.ldpc = torch, ldpc
         self.table = table
+        # the table as raw words: row gathers and pointer patches on plain integers
+        self.words = np.ascontiguousarray(table, dtype=ldpc.work_item_dtype).view(
+            np.uint64).reshape(len(table), ldpc.WORK_ITEM_WORDS)
+        self.w_bits = ldpc.WorkItem.hard_bits.offset // 8
+        self.w_iters = ldpc.WorkItem.iters.offset // 8
         self.ks = ks
         self.early_stop = early_stop
         self.nb = (kmax + 7) // 8
         self.bits = torch.zeros((n_buffers, self.nb), dtype=torch.uint8, device="cuda")
         self.iters = torch.zeros((n_buffers,), dtype=torch.int32, device="cuda")
+        # device address of every output buffer's hard bits and iteration count
+        self.bits_addr = (self.bits.data_ptr()
+                          + np.arange(n_buffers, dtype=np.uint64) * np.uint64(self.nb))
+        self.iters_addr = self.iters.data_ptr() + np.arange(n_buffers, dtype=np.uint64) * 4
         self.n = n_buffers
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.sp = [ctypes.c_void_p(st.cuda_stream) for st in self.streams]
+        self.opts = ldpc.make_opts(ldpc.LLR_INT8, early_stop=early_stop)
         self.clock = torch.cuda.Stream()          # idle stream: slot-boundary timestamps
         self.k = 0
         self.keep = keep_results
         self.results: dict = {}
+        self.ev_pool: list = []
+        self._start = None
         self.learned = learned
         if learned is not None:
             self.nb_l = (learned.graph.K + 7) // 8
             self.bits_l = torch.zeros((n_buffers, self.nb_l), dtype=torch.uint8, device="cuda")
             self.iters_l = torch.zeros((n_buffers,), dtype=torch.int32, device="cuda")
             # learned batches run on streams of their own, concurrently with the slot's
-            # work-list launch; their row maps go up from a pinned ring (a pageable copy
-            # would stall the host until the stream drains)
+            # work-list launch
             self.lstreams = [torch.cuda.Stream() for _ in range(n_streams)]
-            self.ring = 64
-            self.rows_pin = torch.zeros((self.ring, 2, n_buffers), dtype=torch.int32).pin_memory()
-            self.rows_dev = torch.zeros((self.ring, 2, n_buffers), dtype=torch.int32,
-                                        device="cuda")
-            self.ring_ev = [None] * self.ring
+            self.lsp = [ctypes.c_void_p(st.cuda_stream) for st in self.lstreams]
+            self.opts_l = ldpc.make_opts(ldpc.LLR_FP16, algo=ldpc.LEARNED, learned=learned.table,
+                                         n_rows=learned.n_rows, n_tx=learned.pool.shape[1],
+                                         early_stop=early_stop)
+        self._prime()
+
+    def _prime(self):
+        """The library allocates a stream's work table and row-map staging (device and
+        pinned host memory, which can take milliseconds) on that stream's first launch;
+        one throw-away launch per stream here, into output buffer 0, keeps that out of
+        the slots."""
+        z = np.zeros(1, np.int64)
+        for j in range(len(self.streams)):
+            if len(self.words):
+                items = np.take(self.words, z, axis=0)
+                items[:, self.w_bits] = np.take(self.bits_addr, z)
+                items[:, self.w_iters] = np.take(self.iters_addr, z)
+                self.ldpc.decode_list_words(items, stream=self.sp[j], opts=self.opts)
+            lc = self.learned
+            if lc is not None:
+                self.ldpc.decode_rows_host_maps(lc.graph, lc.pool, z, z, lc.max_iter,
+                                                bits=self.bits_l, iters=self.iters_l,
+                                                stream=self.lsp[j], opts=self.opts_l)
+        self.torch.cuda.synchronize()
 
     def capacity(self):
         return self.n
 
+    def _event(self):
+        return self.ev_pool.pop() if self.ev_pool else self.torch.cuda.Event(enable_timing=True)
+
+    def slot_start(self):
+        """Timestamp the slot boundary on the idle stream (the scheduler calls this first
+        thing at every boundary; a slot that admits nothing keeps the event for the next)."""
+        if self._start is None:
+            self._start = self._event()
+        self._start.record(self.clock)
+
     def launch(self, slot, ids, outs):
-        torch = self.torch
-        s = self.streams[self.k % len(self.streams)]
+        if self._start is None:
+            self.slot_start()
+        start, self._start = self._start, None
+        j = self.k % len(self.streams)
         self.k += 1
-        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        start.record(self.clock)
         lc = self.learned
         if lc is not None:
             sel = lc.pick[ids] >= 0
@@ -202,34 +265,19 @@ class GpuBackend:
         else:
             ids_p, outs_p = ids, outs
         if len(ids_p):
-            items = self.table[ids_p].copy()
-            items["hard_bits"] = self.bits.data_ptr() + outs_p * self.nb
-            items["iters"] = self.iters.data_ptr() + outs_p * 4
-            self.ldpc.decode_list_array(items, stream=s, early_stop=self.early_stop)
-        end.record(s)
+            items = np.take(self.words, ids_p, axis=0)
+            items[:, self.w_bits] = np.take(self.bits_addr, outs_p)
+            items[:, self.w_iters] = np.take(self.iters_addr, outs_p)
+            self.ldpc.decode_list_words(items, stream=self.sp[j], opts=self.opts)
+        end = self._event()
+        end.record(self.streams[j])
         end_l = None
         if lc is not None and sel.any():
-            sl = self.lstreams[(self.k - 1) % len(self.lstreams)]
-            r = (self.k - 1) % self.ring
-            if self.ring_ev[r] is not None:
-                self.ring_ev[r].synchronize()          # the copy that last used slot r
-            n = int(sel.sum())
-            pin = self.rows_pin[r].numpy()
-            pin[0, :n] = lc.pick[ids[sel]]
-            pin[1, :n] = outs[sel]
-            dev = self.rows_dev[r]
-            with torch.cuda.stream(sl):
-                dev[:, :n].copy_(self.rows_pin[r][:, :n], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(sl)
-            self.ring_ev[r] = ev
-            self.ldpc.decode_rows(lc.graph, lc.pool, dev[0, :n], dev[1, :n], lc.max_iter,
-                                  bits=self.bits_l, iters=self.iters_l, stream=sl,
-                                  algo=self.ldpc.LEARNED, learned=lc.table,
-                                  n_rows=lc.n_rows, early_stop=self.early_stop,
-                                  check_rows=False)
-            end_l = torch.cuda.Event(enable_timing=True)
-            end_l.record(sl)
+            self.ldpc.decode_rows_host_maps(lc.graph, lc.pool, lc.pick[ids[sel]], outs[sel],
+                                            lc.max_iter, bits=self.bits_l, iters=self.iters_l,
+                                            stream=self.lsp[j], opts=self.opts_l)
+            end_l = self._event()
+            end_l.record(self.lstreams[j])
         return (start, end, end_l)
 
     def done(self, handle):
@@ -257,6 +305,8 @@ class GpuBackend:
         t = start.elapsed_time(end)
         if end_l is not None:
             t = max(t, start.elapsed_time(end_l))
+            self.ev_pool.append(end_l)
+        self.ev_pool += (start, end)
         return t * 1e3
 
 

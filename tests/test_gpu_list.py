@@ -86,6 +86,33 @@ def test_list_back_to_back_and_empty(ldpc):
         g.close()
 
 
+def test_list_words_equals_record_array(ldpc):
+    """The raw-word entry of the work list (the serving path's) decodes the same items as
+    the record-array entry, and rejects arrays of the wrong shape or type."""
+    graphs, items, refs = _mixed(ldpc, 24, 31)
+    arr = np.zeros(len(items), dtype=ldpc.work_item_dtype)
+    for k, (g, llr, bits, it, n_rows, n_tx, T) in enumerate(items):
+        arr[k] = (g.handle.value, llr.data_ptr(), bits.data_ptr(), it.data_ptr(), n_rows,
+                  n_tx, T)
+    ldpc.decode_list_array(arr, early_stop=True)
+    torch.cuda.synchronize()
+    first = [(bits.cpu().numpy().copy(), int(it.item())) for (_, _, bits, it, *_r) in items]
+    for (_, _, bits, it, *_r) in items:
+        bits.zero_()
+        it.zero_()
+    words = arr.view(np.uint64).reshape(len(arr), ldpc.WORK_ITEM_WORDS)
+    ldpc.decode_list_words(np.take(words, np.arange(len(arr)), axis=0), early_stop=True)
+    torch.cuda.synchronize()
+    for (b0, i0), (_, _, bits, it, *_r) in zip(first, items):
+        assert np.array_equal(bits.cpu().numpy(), b0) and int(it.item()) == i0
+    with pytest.raises(ValueError):
+        ldpc.decode_list_words(words[:, :5].copy())
+    with pytest.raises(ValueError):
+        ldpc.decode_list_words(words.astype(np.int64))
+    for g in graphs.values():
+        g.close()
+
+
 def test_list_rejects_unsupported(ldpc):
     wl = make_workload("BG2", 13, 1, 2.0, seed=1)          # odd Z
     g = ldpc.Graph(wl.base, wl.K_b, 13)
@@ -124,4 +151,40 @@ def test_decode_rows_equals_gathered_batch(ldpc, dtype):
         ldpc.decode_rows(g, pool, torch.tensor([40], dtype=torch.int32, device="cuda"),
                          torch.tensor([0], dtype=torch.int32, device="cuda"), 6, bits=bits,
                          iters=iters, **kw)
+    g.close()
+
+
+@pytest.mark.parametrize("dtype", ["int8", "fp16"])
+def test_decode_rows_host_maps_equals_gathered_batch(ldpc, dtype):
+    """Row maps from host memory (the library stages and uploads them): several calls in a
+    row on one stream, the last one larger than the first staging allocation, each equal
+    to decoding its gathered rows as a plain batch; a negative row is rejected."""
+    wl = make_workload("BG2", 64, 300, 1.5, seed=23, graph_seed=0)
+    host = {"int8": wl.llr_int8(), "fp16": wl.llr_fp16()}[dtype]
+    kw = {} if dtype == "int8" else dict(algo=ldpc.NORMALISED, alpha=0.75)
+    g = ldpc.Graph(wl.base, wl.K_b, 64)
+    pool = torch.from_numpy(host).cuda()
+    nb = (wl.K + 7) // 8
+    s = torch.cuda.Stream()
+    rng = np.random.default_rng(9)
+    outs = []
+    for n in (17, 200, 290):
+        in_rows = rng.choice(300, n, replace=False).astype(np.int32)
+        out_rows = rng.permutation(320)[:n].astype(np.int32)
+        bits = torch.zeros((320, nb), dtype=torch.uint8, device="cuda")
+        iters = torch.zeros((320,), dtype=torch.int32, device="cuda")
+        ldpc.decode_rows_host_maps(g, pool, in_rows, out_rows, 8, bits=bits, iters=iters,
+                                   stream=s, **kw)
+        outs.append((bits, iters, in_rows.copy(), out_rows))
+        in_rows[:] = -7                   # the maps are read before the call returns
+    torch.cuda.synchronize()
+    for bits, iters, in_rows, out_rows in outs:
+        ref_b, ref_i = ldpc.decode(g, pool[torch.from_numpy(in_rows).long().cuda()], 8, **kw)
+        assert np.array_equal(bits.cpu().numpy()[out_rows], ref_b.cpu().numpy())
+        assert np.array_equal(iters.cpu().numpy()[out_rows], ref_i.cpu().numpy())
+        untouched = np.setdiff1d(np.arange(320), out_rows)
+        assert (bits.cpu().numpy()[untouched] == 0).all()
+    with pytest.raises(ldpc.LdpcError):
+        ldpc.decode_rows_host_maps(g, pool, np.array([3, -1], np.int32),
+                                   np.array([0, 1], np.int32), 8, bits=bits, iters=iters, **kw)
     g.close()

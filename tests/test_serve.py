@@ -68,6 +68,69 @@ def test_continuous_batching_overlaps_slots():
     assert st["n"] == 24 and st["p99_us"] == 1500.0
 
 
+class _RandomDelayBackend(FakeBackend):
+    """Each batch completes a seeded random number of slots after its launch; slot_start
+    calls are logged in order with the launches."""
+
+    def __init__(self, n_buffers, seed):
+        super().__init__(n_buffers)
+        self.rng = np.random.default_rng(seed)
+        self.log = []
+
+    def slot_start(self):
+        self.log.append("start")
+
+    def launch(self, slot, ids, outs):
+        self.log.append("launch")
+        self.launched.append((slot, ids.tolist(), outs.tolist()))
+        d = int(self.rng.integers(1, 5))
+        return slot + d, d
+
+    def done(self, handle):
+        return self.now >= handle[0]
+
+    def wait(self, handle):
+        self.now = max(self.now, handle[0])
+
+    def finish(self, handle, ids, outs):
+        return handle[1] * self.slot_us
+
+
+class _EagerScheduler(SlotScheduler):
+    """Retires finished batches before every admission."""
+
+    def step(self):
+        self._retire()
+        return super().step()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lazy_retirement_admits_as_eager(seed):
+    """Retiring only when the arena is short (else after the launch) admits the same
+    requests into the same buffers in the same slots as retiring first at every slot, and
+    gives the same latencies; the backend hears of each slot boundary before its launch."""
+    rng = np.random.default_rng(100 + seed)
+    counts = rng.poisson(5, size=60)
+    runs = []
+    for cls in (SlotScheduler, _EagerScheduler):
+        be = _RandomDelayBackend(n_buffers=12, seed=seed)
+        sch = cls(be, slot_us=500.0)
+        for s, n in enumerate(counts):
+            be.now = s
+            sch.submit(int(n))
+            sch.step()
+        sch.drain()
+        runs.append((be, sch))
+    (be_l, sch_l), (be_e, sch_e) = runs
+    assert be_l.launched == be_e.launched
+    assert np.array_equal(sch_l.completed_latencies(), sch_e.completed_latencies())
+    assert sch_l.completed_latencies().size == counts.sum()
+    # the arena ran short: some requests waited for buffers to come back
+    n = sch_l.tail
+    assert (sch_l.admit[:n] > sch_l.arrival[:n]).any()
+    assert all(a == "start" for a, b in zip(be_l.log, be_l.log[1:]) if b == "launch")
+
+
 @pytest.mark.gpu
 def test_results_same_alone_and_in_mix():
     torch = pytest.importorskip("torch")
