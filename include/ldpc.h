@@ -215,6 +215,11 @@ typedef struct {
  * codewords in parallel; the serving path).  int8 offset min-sum with offset_q = 1 and
  * punct_cols = 2 (opts: early_stop is honoured, llr_type must be INT8, algo OFFSET).
  * Each item needs even Z <= 384 and row degrees 2..20 (LDPC_ERR_UNSUPPORTED otherwise).
+ * opts->threads_per_row picks the kernel: 0 (default) the low-latency strategy of Sec. IV
+ * (2 threads per row pair, one persistent block per SM) when every item fits it, else one
+ * thread per row pair; 1 forces the latter, 2 the former (LDPC_ERR_UNSUPPORTED when an
+ * item does not fit it); 4 is LDPC_ERR_UNSUPPORTED, other values LDPC_ERR_INVALID_ARG.
+ * Results are the same whichever kernel runs.
  * Thread blocks take items dynamically, largest first.  The library keeps a per-stream
  * device work table and work counter (allocated on first use, grown on demand, released
  * at exit); the host item array is copied before the call returns, so it may be reused.

@@ -379,12 +379,13 @@ work_item_dtype = np.dtype({
 
 
 def decode_list_array(items: np.ndarray, *, stream=None, early_stop=True,
-                      opts: DecodeOpts | None = None):
+                      opts: DecodeOpts | None = None, threads_per_row=0):
     """ldpc_decode_list on a numpy record array of ``work_item_dtype`` (asynchronous).
     opts: a DecodeOpts from make_opts(LLR_INT8, ...) reused across calls (early_stop is then
     taken from it)."""
     arr = np.ascontiguousarray(items, dtype=work_item_dtype)
-    o = make_opts(LLR_INT8, early_stop=early_stop) if opts is None else opts
+    o = (make_opts(LLR_INT8, early_stop=early_stop, threads_per_row=threads_per_row)
+         if opts is None else opts)
     _check(lib().ldpc_decode_list(arr.ctypes.data_as(ctypes.POINTER(WorkItem)), len(arr),
                                   _stream_ptr(stream), ctypes.byref(o)), "ldpc_decode_list")
 
@@ -393,7 +394,7 @@ WORK_ITEM_WORDS = ctypes.sizeof(WorkItem) // 8
 
 
 def decode_list_words(words: np.ndarray, *, stream=None, early_stop=True,
-                      opts: DecodeOpts | None = None):
+                      opts: DecodeOpts | None = None, threads_per_row=0):
     """ldpc_decode_list on work items held as raw 64-bit words: a C-contiguous uint64 array
     [n][WORK_ITEM_WORDS] laid out byte for byte as ``ldpc_work_item`` (e.g.
     ``items.view(np.uint64).reshape(n, -1)`` of a ``work_item_dtype`` array).  Gathering
@@ -402,26 +403,31 @@ def decode_list_words(words: np.ndarray, *, stream=None, early_stop=True,
     if (words.dtype != np.uint64 or words.ndim != 2 or words.shape[1] != WORK_ITEM_WORDS
             or not words.flags.c_contiguous):
         raise ValueError("work items must be a C-contiguous uint64 [n][WORK_ITEM_WORDS] array")
-    o = make_opts(LLR_INT8, early_stop=early_stop) if opts is None else opts
+    o = (make_opts(LLR_INT8, early_stop=early_stop, threads_per_row=threads_per_row)
+         if opts is None else opts)
     _check(lib().decode_list_words(words.ctypes.data, words.shape[0], _stream_ptr(stream),
                                    ctypes.byref(o)), "ldpc_decode_list")
 
 
-def decode_list(items, *, stream=None, early_stop=True):
+def decode_list(items, *, stream=None, early_stop=True, threads_per_row=0):
     """Decode a heterogeneous list in one launch (ldpc_decode_list).
 
     items: sequence of (graph, llr int8 CUDA tensor [n_tx], bits uint8 CUDA tensor
     [ceil(K/8)], iters int32 CUDA tensor [1], n_rows, n_tx, max_iter).  Outputs are written
-    in place; the call is asynchronous on the stream.
+    in place; the call is asynchronous on the stream.  threads_per_row: 0 picks the
+    kernel (2 threads per row pair, messages in Tensor Memory, when every item allows it),
+    1 forces the one-thread-per-row-pair list kernel, 2 the low-latency one.
     """
     arr = np.zeros(len(items), dtype=work_item_dtype)
     for k, (g, llr, bits, it, n_rows, n_tx, max_iter) in enumerate(items):
         arr[k] = (g.handle.value, llr.data_ptr(), bits.data_ptr(), it.data_ptr(), int(n_rows),
                   int(n_tx), int(max_iter))
-    decode_list_array(arr, stream=stream, early_stop=early_stop)
+    decode_list_array(arr, stream=stream, early_stop=early_stop,
+                      threads_per_row=threads_per_row)
 
 
-def decode_list_noalloc(items: np.ndarray, *, stream=None, early_stop=True):
+def decode_list_noalloc(items: np.ndarray, *, stream=None, early_stop=True,
+                        threads_per_row=0):
     """ldpc_decode_list_noalloc on a numpy record array of ``work_item_dtype``.
 
     For callers that cannot allocate device memory: the library allocates nothing on this
@@ -429,7 +435,7 @@ def decode_list_noalloc(items: np.ndarray, *, stream=None, early_stop=True):
     array shared by every call, so calls must not overlap on the GPU.  The first call on a
     device looks the array up and should come before any stream capture."""
     arr = np.ascontiguousarray(items, dtype=work_item_dtype)
-    o = make_opts(LLR_INT8, early_stop=early_stop)
+    o = make_opts(LLR_INT8, early_stop=early_stop, threads_per_row=threads_per_row)
     _check(lib().ldpc_decode_list_noalloc(arr.ctypes.data_as(ctypes.POINTER(WorkItem)), len(arr),
                                           _stream_ptr(stream), ctypes.byref(o)),
            "ldpc_decode_list_noalloc")

@@ -416,7 +416,7 @@ ListItem g_noalloc_host[kNoAllocMaxItems];        // host staging of the sorted 
 }  // namespace
 
 ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t smem,
-                                int early_stop, cudaStream_t stream) {
+                                int early_stop, bool ll, cudaStream_t stream) {
     if (n_items < 0 || n_items > kNoAllocMaxItems) return LDPC_ERR_INVALID_ARG;
     if (n_items == 0) return LDPC_OK;
     int dev = 0;
@@ -439,7 +439,8 @@ ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t sme
                         cudaMemcpyHostToDevice, stream) != cudaSuccess ||
         cudaMemsetAsync(&d->counter, 0, sizeof(int), stream) != cudaSuccess)
         return LDPC_ERR_CUDA;
-    return launch_list(d->items, n_items, &d->counter, smem, early_stop, stream);
+    return ll ? launch_list_ll(d->items, n_items, &d->counter, smem, early_stop, stream)
+              : launch_list(d->items, n_items, &d->counter, smem, early_stop, stream);
 }
 
 }  // namespace ldpc

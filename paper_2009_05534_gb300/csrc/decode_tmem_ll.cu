@@ -415,4 +415,214 @@ ldpc_status launch_tmem_ll(const DecodeParams &p, int A, cudaStream_t stream) {
     return LDPC_OK;
 }
 
+// ------------------------------------------------------------ work list, low latency
+//
+// The same strategy for a heterogeneous work list (items of different graphs, lifting
+// sizes and rates in one launch): one persistent block of kThreadsLL threads per SM claims
+// items from a counter and decodes each with alpha = 2 threads per row pair.  An item's
+// graph tables (gather metadata, row offsets, TMEM slot offsets) are built in shared
+// memory when the block takes it, from the graph's device edge table; the warps beyond the
+// item's 2 * Z/2 threads only take part in the barriers.  The item's channel LLRs are
+// staged in shared memory by 16-byte loads of the aligned part of the row (all in flight
+// at once) and byte loads of its ragged ends, then spread into the posterior words.
+
+namespace {
+
+constexpr int kThreadsLL = 384;          // alpha * Z / 2 for Z <= 384
+
+__device__ __forceinline__ EdgeMetaL meta_l(uint32_t edge, int H) {
+    const int c = (int)(edge >> 16), sh = (int)(edge & 0xffffu);
+    const int q = sh >= H ? 1 : 0, u = sh - q * H;
+    EdgeMetaL m;
+    m.base_nw = c * H + u;
+    m.thresh = H - u;
+    m.sel_nw = q ? 0x1032u : 0x3210u;
+    m.sel_w = q ? 0x3210u : 0x1032u;
+    return m;
+}
+
+__global__ void __launch_bounds__(kThreadsLL, 1)
+    list_ll_kernel(const ListItem *__restrict__ items, int n_items, int *counter,
+                   int early_stop) {
+    constexpr int A = 2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tmem_base;
+    __shared__ int s_idx, s_stop[2];
+    __shared__ int s_row[kMaxRowsL + 1], s_slot[kMaxRowsL + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x;
+    const int k = tid % A;
+    EdgeMetaL *s_meta = reinterpret_cast<EdgeMetaL *>(smem);
+
+    if (warp == 0) tmem_alloc(&s_tmem_base, kTmemColsL);
+    tmem_block_sync();
+#pragma unroll 1
+    for (;;) {
+        if (tid == 0) s_idx = atomicAdd(counter, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= n_items) break;
+        const ListItem it = items[idx];
+        const int Z = it.Z, H = Z / 2, E = it.E, n_rows = it.n_rows, n_cols = it.n_cols;
+        const int off_lb = (int)(((size_t)E * sizeof(EdgeMetaL) + 15) & ~(size_t)15);
+        const int off_stage = (off_lb + n_cols * H * 4 + 15) & ~15;
+        uint32_t *Lb = reinterpret_cast<uint32_t *>(smem + off_lb);
+        // LLR byte t of the item sits at S[t]: the 16-byte words of the row that lie wholly
+        // inside it land on 16-byte boundaries of the staging area
+        const int n_tx = it.n_tx;
+        const int hd = (int)((16u - ((uint32_t)reinterpret_cast<uintptr_t>(it.llr) & 15u)) & 15u);
+        const int n16 = n_tx > hd ? (n_tx - hd) >> 4 : 0;      // whole 16-byte words
+        int8_t *S = reinterpret_cast<int8_t *>(smem + off_stage) + 16 - hd;
+        {
+            const int4 *src4 = reinterpret_cast<const int4 *>(it.llr + hd);
+            int4 *dst4 = reinterpret_cast<int4 *>(S + hd);
+            for (int i0 = tid; i0 < n16; i0 += 4 * nthr) {   // four loads in flight
+                int4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * nthr < n16) v[u] = __ldg(src4 + i0 + u * nthr);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * nthr < n16) dst4[i0 + u * nthr] = v[u];
+            }
+        }
+        for (int t = tid; t < hd && t < n_tx; t += nthr) S[t] = it.llr[t];
+        for (int t = hd + 16 * n16 + tid; t < n_tx; t += nthr) S[t] = it.llr[t];
+        for (int e = tid; e < E; e += nthr) s_meta[e] = meta_l(it.edges[e], H);
+        for (int r = tid; r <= n_rows; r += nthr) s_row[r] = it.row_ptr[r];
+        __syncthreads();
+        // a0: biased posteriors from the channel LLRs (word (c, j): rows j and j + H); the
+        // block splits into nthr / H groups of H threads, group g taking columns g, g + G, ..
+        {
+            const int lo = it.punct * Z, G = nthr / H, g = tid / H, j = tid - g * H;
+            if (g < G)
+                for (int c = g; c < n_cols; c += G) {
+                    const int t0 = c * Z + j - lo, t1 = t0 + H;
+                    const int q0 = (t0 >= 0 && t0 < n_tx) ? (int)S[t0] : 0;
+                    const int q1 = (t1 >= 0 && t1 < n_tx) ? (int)S[t1] : 0;
+                    Lb[c * H + j] = (uint32_t)(0x64FF + q0) | ((uint32_t)(0x64FF + q1) << 16);
+                }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int sl = 0;
+            for (int r = 0; r < n_rows; ++r) {
+                s_slot[r] = sl;
+                sl += (s_row[r + 1] - s_row[r] + A - 1) / A;
+            }
+            s_slot[n_rows] = sl;
+            s_stop[0] = s_stop[1] = 0;
+        }
+        __syncthreads();
+        const int ncols = (s_slot[n_rows] + 1) / 2;
+        // warps holding at least one real row pair; the rest only meet the barriers
+        const bool active = warp * 32 < A * H;
+        const bool store = tid / A < H;
+        const int w = store ? tid / A : H - 1;          // spare threads shadow the last pair
+        const uint32_t tbase = s_tmem_base + ((uint32_t)((warp & 3) * 32) << 16) +
+                               (uint32_t)((warp >> 2) * ncols);
+        if (active) {                                   // zero messages (bytes c + 128)
+            uint32_t z[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) z[q] = 0x80808080u;
+            int c = 0;
+            for (; c + 8 <= ncols; c += 8) tst<8>(tbase + c, z);
+            for (; c < ncols; ++c) tst<1>(tbase + c, z);
+        }
+        int r_scan = 0;
+        int done = it.max_iter;
+#pragma unroll 1
+        for (int t = 1; t <= it.max_iter; ++t) {
+#pragma unroll 1
+            for (int r = 0; r < n_rows; ++r) {
+                const int e0 = s_row[r];
+                if (active)
+                    ll_dispatch<A>(s_row[r + 1] - e0, s_meta, Lb, tbase, s_slot[r], e0, H, w,
+                                   k, store);
+                named_sync(1, nthr);
+            }
+            if (early_stop) {
+                volatile int *vstop = &s_stop[t & 1];
+                int bad = 0;
+                if (active) {
+                    int r = r_scan;
+                    for (int q = 0; q < n_rows && !bad && !*vstop;
+                         ++q, r = (r + 1 == n_rows) ? 0 : r + 1) {
+                        const int e0 = s_row[r];
+                        bad = __any_sync(0xffffffffu,
+                                         ll_parity<A>(s_meta, Lb, e0, s_row[r + 1] - e0, H, w,
+                                                      k) != 0u);
+                        if (bad) {
+                            if ((tid & 31) == 0) *vstop = 1;
+                            r_scan = r;
+                        }
+                    }
+                }
+                const int any = named_or(1, nthr, bad);
+                if (tid == 0) s_stop[(t + 1) & 1] = 0;
+                if (any == 0) {
+                    done = t;
+                    break;
+                }
+            }
+        }
+        // a6: outputs
+        const int K = it.K_b * Z, nbytes = (K + 7) >> 3;
+        for (int b = tid; b < nbytes; b += nthr) {
+            unsigned x = 0;
+            for (int kk = 0; kk < 8; ++kk) {
+                const int j = 8 * b + kk;
+                if (j >= K) break;
+                const int c = j / Z, i = j - c * Z;
+                const int lane = i >= H ? 1 : 0;
+                const uint32_t wd = Lb[c * H + i - lane * H];
+                const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
+                if (h < 0x64FFu) x |= 1u << kk;
+            }
+            it.bits[b] = (uint8_t)x;
+        }
+        if (tid == 0) it.iters[0] = done;
+        // the next item places its TMEM regions and shared tables differently: every
+        // thread's message stores and table reads of this item end here
+        if (active) twait_st();
+        tmem_block_sync();
+    }
+    tmem_block_sync();
+    if (warp == 0) tmem_dealloc(s_tmem_base, kTmemColsL);
+}
+
+}  // namespace
+
+bool list_ll_item_supported(int Z, int E, int n_rows, int max_deg, int slots2) {
+    if ((Z & 1) || Z < 2 || Z > kThreadsLL || max_deg < 2 || max_deg > kMaxDeg) return false;
+    if (E > kMaxEdgesL || n_rows > kMaxRowsL) return false;
+    const int nwarps = (Z + 31) / 32;                // alpha * Z / 2 threads, alpha = 2
+    const int depth = (nwarps + 3) / 4;
+    return depth * ((slots2 + 1) / 2) <= kTmemColsL;
+}
+
+size_t list_ll_smem_bytes(int E, int n_cols, int Z, int n_tx) {
+    const size_t off = ((size_t)E * sizeof(EdgeMetaL) + 15) & ~(size_t)15;
+    const size_t stage = (off + (size_t)n_cols * (Z / 2) * 4 + 15) & ~(size_t)15;
+    return stage + 16 + (size_t)n_tx + 16;
+}
+
+ldpc_status launch_list_ll(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
+                           int early_stop, cudaStream_t stream) {
+    int dev = 0, n_sm = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // at least 120 kB so that one block occupies the SM (its TMEM allocation takes all 512
+    // columns; a second block would wait in the allocation)
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    if (smem > (size_t)optin) return LDPC_ERR_UNSUPPORTED;
+    if (set_dyn_smem(reinterpret_cast<const void *>(list_ll_kernel), smem) != cudaSuccess)
+        return LDPC_ERR_CUDA;
+    const int grid = n_items < n_sm ? n_items : n_sm;
+    list_ll_kernel<<<grid, kThreadsLL, smem, stream>>>(d_items, n_items, d_counter, early_stop);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
 }  // namespace ldpc

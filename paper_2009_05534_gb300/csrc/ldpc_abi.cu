@@ -138,12 +138,13 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
     g->Z = Z;
     g->E_total = E;
     uint32_t *h_edges = g->h_edges;
-    int e = 0, maxc = -1, maxd = 0, mind = 1 << 30;
+    int e = 0, maxc = -1, maxd = 0, mind = 1 << 30, slots2 = 0;
     for (int r = 0; r < M_bg; ++r) {
         g->row_ptr[r] = e;
         g->max_col_upto[r] = maxc;
         g->max_deg_upto[r] = maxd;
         g->min_deg_upto[r] = mind;
+        g->slots2_upto[r] = slots2;
         int d = 0;
         for (int c = 0; c < N_bg; ++c) {
             const int v = base[r * N_bg + c];
@@ -154,7 +155,9 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
         }
         if (d > maxd) maxd = d;
         if (d < mind) mind = d;
+        slots2 += (d + 1) / 2;
     }
+    g->slots2_upto[M_bg] = slots2;
     g->row_ptr[M_bg] = e;
     g->max_col_upto[M_bg] = maxc;
     g->max_deg_upto[M_bg] = maxd;
@@ -524,12 +527,17 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
     if (o.llr_type != LDPC_LLR_INT8 || o.algo != LDPC_OFFSET || o.offset_q != 1 ||
         o.punct_cols != 2 || o.cluster_size != 1)
         return LDPC_ERR_UNSUPPORTED;
+    if (o.threads_per_row < 0 || o.threads_per_row > 4 || o.threads_per_row == 3)
+        return LDPC_ERR_INVALID_ARG;
+    if (o.threads_per_row == 4) return LDPC_ERR_UNSUPPORTED;
     if (n_items == 0) return LDPC_OK;
-    int dev = 0;
+    int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     std::vector<std::pair<double, ldpc::ListItem>> v;
     v.reserve((size_t)n_items);
-    size_t smem = 0;
+    size_t smem = 0, smem_ll = 0;
+    bool ll_ok = o.threads_per_row != 1;
     for (int k = 0; k < n_items; ++k) {
         const ldpc_work_item &w = items[k];
         if (!w.graph || !w.llr || !w.hard_bits || !w.iters) return LDPC_ERR_INVALID_ARG;
@@ -561,8 +569,13 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
         it.punct = 2;
         it.max_iter = w.max_iter;
         smem = std::max(smem, ldpc::list_item_smem_bytes(E, n_rows, n_cols, g->Z));
+        ll_ok = ll_ok && ldpc::list_ll_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows],
+                                                      g->slots2_upto[n_rows]);
+        smem_ll = std::max(smem_ll, ldpc::list_ll_smem_bytes(E, n_cols, g->Z, n_tx));
         v.emplace_back((double)E * g->Z * w.max_iter, it);
     }
+    ll_ok = ll_ok && smem_ll <= (size_t)optin;
+    if (o.threads_per_row == 2 && !ll_ok) return LDPC_ERR_UNSUPPORTED;
     // largest items first: the dynamic work counter then balances the tail
     std::stable_sort(v.begin(), v.end(),
                      [](const auto &a, const auto &b) { return a.first > b.first; });
@@ -603,6 +616,9 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
         cudaEventRecord(ws.copied, s) != cudaSuccess ||
         cudaMemsetAsync(ws.d_counter, 0, sizeof(int), s) != cudaSuccess)
         return LDPC_ERR_CUDA;
+    if (ll_ok)
+        return ldpc::launch_list_ll(ws.d_items, n_items, ws.d_counter, smem_ll,
+                                    o.early_stop ? 1 : 0, s);
     return ldpc::launch_list(ws.d_items, n_items, ws.d_counter, smem, o.early_stop ? 1 : 0, s);
 }
 
@@ -610,7 +626,8 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
 // fixed arrays and the launch order (largest work first) into order[0..n).
 static ldpc_status prepare_list_noalloc(const ldpc_work_item *items, int n_items,
                                 const ldpc_decode_opts *opts, ldpc::ListItem *out,
-                                int *order, double *work, size_t *smem_out, int *early_stop) {
+                                int *order, double *work, size_t *smem_out, int *early_stop,
+                                size_t *smem_ll_out, bool *ll_out) {
     ldpc_decode_opts o;
     if (opts)
         o = *opts;
@@ -619,10 +636,15 @@ static ldpc_status prepare_list_noalloc(const ldpc_work_item *items, int n_items
     if (o.llr_type != LDPC_LLR_INT8 || o.algo != LDPC_OFFSET || o.offset_q != 1 ||
         o.punct_cols != 2 || o.cluster_size != 1)
         return LDPC_ERR_UNSUPPORTED;
+    if (o.threads_per_row < 0 || o.threads_per_row > 4 || o.threads_per_row == 3)
+        return LDPC_ERR_INVALID_ARG;
+    if (o.threads_per_row == 4) return LDPC_ERR_UNSUPPORTED;
     *early_stop = o.early_stop ? 1 : 0;
-    int dev = 0;
+    int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
-    size_t smem = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    size_t smem = 0, smem_ll = 0;
+    bool ll_ok = o.threads_per_row != 1;
     for (int k = 0; k < n_items; ++k) {
         const ldpc_work_item &w = items[k];
         if (!w.graph || !w.llr || !w.hard_bits || !w.iters) return LDPC_ERR_INVALID_ARG;
@@ -654,6 +676,9 @@ static ldpc_status prepare_list_noalloc(const ldpc_work_item *items, int n_items
         it.punct = 2;
         it.max_iter = w.max_iter;
         smem = std::max(smem, ldpc::list_item_smem_bytes(E, n_rows, n_cols, g->Z));
+        ll_ok = ll_ok && ldpc::list_ll_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows],
+                                                      g->slots2_upto[n_rows]);
+        smem_ll = std::max(smem_ll, ldpc::list_ll_smem_bytes(E, n_cols, g->Z, n_tx));
         order[k] = k;
         work[k] = (double)E * g->Z * w.max_iter;
     }
@@ -662,7 +687,11 @@ static ldpc_status prepare_list_noalloc(const ldpc_work_item *items, int n_items
     std::sort(order, order + n_items, [work](int a, int b) {
         return work[a] > work[b] || (work[a] == work[b] && a < b);
     });
+    ll_ok = ll_ok && smem_ll <= (size_t)optin;
+    if (o.threads_per_row == 2 && !ll_ok) return LDPC_ERR_UNSUPPORTED;
     *smem_out = smem;
+    *smem_ll_out = smem_ll;
+    *ll_out = ll_ok;
     return LDPC_OK;
 }
 
@@ -677,12 +706,14 @@ ldpc_status ldpc_decode_list_noalloc(const ldpc_work_item *items, int n_items,
     static int order[ldpc::kNoAllocMaxItems];
     static double work[ldpc::kNoAllocMaxItems];
     std::lock_guard<std::mutex> lk(mu);
-    size_t smem = 0;
+    size_t smem = 0, smem_ll = 0;
     int early_stop = 1;
-    ldpc_status st = prepare_list_noalloc(items, n_items, opts, raw, order, work, &smem, &early_stop);
+    bool ll = false;
+    ldpc_status st = prepare_list_noalloc(items, n_items, opts, raw, order, work, &smem,
+                                          &early_stop, &smem_ll, &ll);
     if (st != LDPC_OK) return st;
     for (int k = 0; k < n_items; ++k) sorted[k] = raw[order[k]];
-    return ldpc::launch_list_noalloc(sorted, n_items, smem, early_stop,
+    return ldpc::launch_list_noalloc(sorted, n_items, ll ? smem_ll : smem, early_stop, ll,
                                      reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -23,6 +23,7 @@ struct Graph {
     int max_col_upto[kMaxRows + 1] = {}; // largest column referenced by rows < r
     int max_deg_upto[kMaxRows + 1] = {}; // largest row degree among rows < r
     int min_deg_upto[kMaxRows + 1] = {}; // smallest row degree among rows < r
+    int slots2_upto[kMaxRows + 1] = {};  // sum of ceil(degree / 2) over rows < r
     uint32_t h_edges[kMaxEdges] = {};    // (column << 16) | (shift mod Z), row by row
     uint32_t *d_edges = nullptr;         // device copy of h_edges
     int *d_row_ptr = nullptr;            // device [M_bg + 1]
@@ -141,14 +142,21 @@ ldpc_status launch_learned(const DecodeParams &dp, int T, const float *params, c
 // which must be zero at launch.
 bool list_item_supported(int Z, int E, int n_rows, int max_deg);
 size_t list_item_smem_bytes(int E, int n_rows, int n_cols, int Z);
+// The work list with the low-latency strategy (decode_tmem_ll.cu): alpha = 2 threads per
+// row pair, messages in Tensor Memory; slots2 = sum of ceil(degree / 2) over the item's rows.
+bool list_ll_item_supported(int Z, int E, int n_rows, int max_deg, int slots2);
+size_t list_ll_smem_bytes(int E, int n_cols, int Z, int n_tx);
+ldpc_status launch_list_ll(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
+                           int early_stop, cudaStream_t stream);
 ldpc_status launch_list(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
                         int early_stop, cudaStream_t stream);
 
 // Work-list decode whose work table and counter sit in a static device array
-// (decode_rowpair.cu); h_items is sorted host-side already.
+// (decode_rowpair.cu); h_items is sorted host-side already; ll selects the low-latency
+// list kernel (smem is then its request).
 constexpr int kNoAllocMaxItems = 2048;
 ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t smem,
-                                int early_stop, cudaStream_t stream);
+                                int early_stop, bool ll, cudaStream_t stream);
 
 void count_launch();
 

@@ -48,10 +48,13 @@ def _mixed(ldpc, n, seed):
     return graphs, items, refs
 
 
+@pytest.mark.parametrize("tpr", [1, 2])
 @pytest.mark.parametrize("early_stop", [False, True])
-def test_list_matches_oracle_and_alone(ldpc, early_stop):
+def test_list_matches_oracle_and_alone(ldpc, early_stop, tpr):
+    """Each list kernel (tpr 1: one thread per row pair; 2: the low-latency one) against
+    the oracle, and against the same codeword decoded alone."""
     graphs, items, refs = _mixed(ldpc, 40, 100 + int(early_stop))
-    ldpc.decode_list(items, early_stop=early_stop)
+    ldpc.decode_list(items, early_stop=early_stop, threads_per_row=tpr)
     torch.cuda.synchronize()
     for (g, llr, bits, it, n_rows, n_tx, T), (wl, q, _) in zip(items, refs):
         ref = oracle.decode_layered(wl.base, wl.K_b, wl.Z, wl.n_rows, q, algo=oracle.OFFSET,
@@ -69,14 +72,15 @@ def test_list_matches_oracle_and_alone(ldpc, early_stop):
         g.close()
 
 
-def test_list_back_to_back_and_empty(ldpc):
+@pytest.mark.parametrize("tpr", [0, 1, 2])
+def test_list_back_to_back_and_empty(ldpc, tpr):
     graphs, items, refs = _mixed(ldpc, 12, 7)
-    ldpc.decode_list([])
+    ldpc.decode_list([], threads_per_row=tpr)
     for _ in range(3):                    # reuse of the per-stream work table
         for (_, _, bits, it, *_r) in items:
             bits.zero_()
             it.zero_()
-        ldpc.decode_list(items, early_stop=False)
+        ldpc.decode_list(items, early_stop=False, threads_per_row=tpr)
     torch.cuda.synchronize()
     for (g, llr, bits, it, n_rows, n_tx, T), (wl, q, _) in zip(items, refs):
         ref = oracle.decode_layered(wl.base, wl.K_b, wl.Z, wl.n_rows, q, algo=oracle.OFFSET,
@@ -111,6 +115,76 @@ def test_list_words_equals_record_array(ldpc):
         ldpc.decode_list_words(words.astype(np.int64))
     for g in graphs.values():
         g.close()
+
+
+def test_list_small_lifting_sizes_and_many_items(ldpc):
+    """Lifting sizes down to 2 (a single row pair: one busy warp, the rest of the block at
+    the barriers only) and more items than SMs (blocks take several items in turn), low-
+    latency list kernel against the one-thread kernel and the oracle."""
+    rng = np.random.default_rng(77)
+    graphs, items, refs = {}, [], []
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    for k in range(n_sm + 40):
+        Z = int(rng.choice([2, 4, 6, 10, 36, 384]))
+        kind = "BG1" if rng.integers(2) else "BG2"
+        wl = make_workload(kind, Z, 1, float(rng.uniform(0.0, 4.0)), seed=500 + k,
+                           graph_seed=0)
+        if (kind, Z) not in graphs:
+            graphs[(kind, Z)] = ldpc.Graph(wl.base, wl.K_b, Z)
+        q = wl.llr_int8()
+        llr = torch.from_numpy(q[0]).cuda()
+        bits = torch.zeros(((wl.K + 7) // 8,), dtype=torch.uint8, device="cuda")
+        it = torch.zeros((1,), dtype=torch.int32, device="cuda")
+        items.append((graphs[(kind, Z)], llr, bits, it, wl.n_rows, wl.n_tx, 6))
+        refs.append((wl, q))
+    outs = {}
+    for tpr in (1, 2):
+        for (_, _, bits, it, *_r) in items:
+            bits.zero_()
+            it.zero_()
+        ldpc.decode_list(items, early_stop=True, threads_per_row=tpr)
+        torch.cuda.synchronize()
+        outs[tpr] = [(bits.cpu().numpy().copy(), int(it.item())) for (_, _, bits, it, *_r) in items]
+    for k, ((wl, q), (b2, i2)) in enumerate(zip(refs, outs[2])):
+        assert np.array_equal(b2, outs[1][k][0]) and i2 == outs[1][k][1]
+        if k % 8 == 0:
+            ref = oracle.decode_layered(wl.base, wl.K_b, wl.Z, wl.n_rows, q, algo=oracle.OFFSET,
+                                        max_iter=6, early_stop=True)
+            assert np.array_equal(ldpc.unpack_bits(b2[None, :], wl.K), ref.bits)
+            assert i2 == int(ref.iters[0])
+    for g in graphs.values():
+        g.close()
+
+
+def test_list_dense_graph_falls_back(ldpc):
+    """A graph whose messages do not fit the low-latency kernel's Tensor Memory at two
+    threads per row pair (52 rows of degree 19 at Z = 160: 520 slots, two warps per lane
+    quarter) decodes through the one-thread kernel by default; asking for the low-latency
+    kernel is refused, and so are 3 (invalid) and 4 threads per row pair (unsupported)."""
+    rng = np.random.default_rng(3)
+    M, K_b, Z = 52, 20, 160
+    base = np.full((M, K_b + M), -1, np.int16)
+    for r in range(M):
+        cols = rng.choice(K_b + M, 19, replace=False)
+        base[r, cols] = rng.integers(0, Z, 19)
+    g = ldpc.Graph(base, K_b, Z)
+    n_tx = (K_b + M - 2) * Z
+    llr = torch.from_numpy(rng.integers(-20, 21, size=n_tx).astype(np.int8)).cuda()
+    res = {}
+    for tpr in (0, 1):
+        bits = torch.zeros(((K_b * Z + 7) // 8,), dtype=torch.uint8, device="cuda")
+        it = torch.zeros((1,), dtype=torch.int32, device="cuda")
+        ldpc.decode_list([(g, llr, bits, it, M, n_tx, 5)], early_stop=False, threads_per_row=tpr)
+        torch.cuda.synchronize()
+        res[tpr] = (bits.cpu().numpy(), int(it.item()))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] == 5
+    ref = oracle.decode_layered(base, K_b, Z, M, llr.cpu().numpy()[None, :], algo=oracle.OFFSET,
+                                max_iter=5, early_stop=False)
+    assert np.array_equal(ldpc.unpack_bits(res[0][0][None, :], K_b * Z), ref.bits)
+    for tpr in (2, 3, 4):
+        with pytest.raises(ldpc.LdpcError):
+            ldpc.decode_list([(g, llr, bits, it, M, n_tx, 5)], threads_per_row=tpr)
+    g.close()
 
 
 def test_list_rejects_unsupported(ldpc):

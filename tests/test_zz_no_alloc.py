@@ -44,7 +44,7 @@ def _items(ldpc, n, seed):
     return graphs, keep, table
 
 
-def _run(ldpc, table, noalloc, early_stop):
+def _run(ldpc, table, noalloc, early_stop, tpr=0):
     n = len(table)
     nb = 1056
     bits = torch.zeros((n, nb), dtype=torch.uint8, device="cuda")
@@ -53,19 +53,22 @@ def _run(ldpc, table, noalloc, early_stop):
     t["hard_bits"] = bits.data_ptr() + np.arange(n) * nb
     t["iters"] = iters.data_ptr() + np.arange(n) * 4
     if noalloc:
-        ldpc.decode_list_noalloc(t, early_stop=early_stop)
+        ldpc.decode_list_noalloc(t, early_stop=early_stop, threads_per_row=tpr)
     else:
-        ldpc.decode_list_array(t, early_stop=early_stop)
+        ldpc.decode_list_array(t, early_stop=early_stop, threads_per_row=tpr)
     torch.cuda.synchronize()
     return bits.cpu().numpy(), iters.cpu().numpy()
 
 
+@pytest.mark.parametrize("tpr", [1, 2])
 @pytest.mark.parametrize("early_stop", [True, False])
-def test_noalloc_matches_list_decode_twice(ldpc, early_stop):
+def test_noalloc_matches_list_decode_twice(ldpc, early_stop, tpr):
+    """Both list kernels (one and two threads per row pair) through the allocation-free
+    entry equal the regular entry's one-thread kernel."""
     graphs, keep, table = _items(ldpc, 48, 900 + int(early_stop))
-    ref_bits, ref_iters = _run(ldpc, table, False, early_stop)
+    ref_bits, ref_iters = _run(ldpc, table, False, early_stop, tpr=1)
     for _ in range(2):                            # two calls in a row reuse the static table
-        b, it = _run(ldpc, table, True, early_stop)
+        b, it = _run(ldpc, table, True, early_stop, tpr)
         assert np.array_equal(b, ref_bits)        # bit-exact, like every int8 path
         assert np.array_equal(it, ref_iters)
     for g in graphs.values():
