@@ -331,13 +331,15 @@ __global__ void __launch_bounds__(384, 1) tmem16_kernel(const __grid_constant__ 
                 // a6: outputs
                 for (int b = ht; b < nbytes; b += nthr_half) {
                     unsigned x = 0;
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const int j = 8 * b + kk;
-                        if (j >= K) break;
-                        const int c = j / Z, i = j - c * Z;
+                    int c = (8 * b) / Z, i = 8 * b - c * Z;    // bit j = c Z + i, stepped
+                    for (int kk = 0; kk < 8 && 8 * b + kk < K; ++kk) {
                         const int lane = i >= H ? 1 : 0;
                         const uint32_t wd = Lb[c * H + i - lane * H];
                         if ((lane ? (wd >> 31) : (wd >> 15)) & 1u) x |= 1u << kk;
+                        if (++i == Z) {
+                            i = 0;
+                            ++c;
+                        }
                     }
                     p.bits[out_row(p, cw) * nbytes + b] = (uint8_t)x;
                 }

@@ -285,14 +285,16 @@ __global__ void __launch_bounds__(A * 192, 1) tmem_ll_kernel(const __grid_consta
         // a6: outputs
         for (int b = tid; b < nbytes; b += nthr) {
             unsigned x = 0;
-            for (int kk = 0; kk < 8; ++kk) {
-                const int j = 8 * b + kk;
-                if (j >= K) break;
-                const int c = j / Z, i = j - c * Z;
+            int c = (8 * b) / Z, i = 8 * b - c * Z;            // bit j = c Z + i, stepped
+            for (int kk = 0; kk < 8 && 8 * b + kk < K; ++kk) {
                 const int lane = i >= H ? 1 : 0;
                 const uint32_t wd = Lb[c * H + i - lane * H];
                 const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
                 if (h < 0x64FFu) x |= 1u << kk;
+                if (++i == Z) {
+                    i = 0;
+                    ++c;
+                }
             }
             p.bits[out_row(p, cw) * nbytes + b] = (uint8_t)x;
         }
@@ -569,14 +571,16 @@ __global__ void __launch_bounds__(kThreadsLL, 1)
         const int K = it.K_b * Z, nbytes = (K + 7) >> 3;
         for (int b = tid; b < nbytes; b += nthr) {
             unsigned x = 0;
-            for (int kk = 0; kk < 8; ++kk) {
-                const int j = 8 * b + kk;
-                if (j >= K) break;
-                const int c = j / Z, i = j - c * Z;
+            int c = (8 * b) / Z, i = 8 * b - c * Z;            // bit j = c Z + i, stepped
+            for (int kk = 0; kk < 8 && 8 * b + kk < K; ++kk) {
                 const int lane = i >= H ? 1 : 0;
                 const uint32_t wd = Lb[c * H + i - lane * H];
                 const uint32_t h = lane ? (wd >> 16) : (wd & 0xffffu);
                 if (h < 0x64FFu) x |= 1u << kk;
+                if (++i == Z) {
+                    i = 0;
+                    ++c;
+                }
             }
             it.bits[b] = (uint8_t)x;
         }

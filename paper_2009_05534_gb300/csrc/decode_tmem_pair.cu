@@ -290,13 +290,19 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
     };
     // a6 for lane X: hard bits, iteration count, and the debug outputs
     auto emit = [&](int X) {
+        // byte b packs the hard decisions of posterior words 8b .. 8b + 7 (32 bytes, read as
+        // two 16-byte words); words past K exist (parity columns follow) and are masked off
+        const int sh = 16 * X;
         for (int b = tid; b < nbytes; b += nthr) {
+            const uint4 q0 = reinterpret_cast<const uint4 *>(Lb)[2 * b];
+            const uint4 q1 = reinterpret_cast<const uint4 *>(Lb)[2 * b + 1];
+            const uint32_t wv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
             unsigned x = 0;
-            for (int kk = 0; kk < 8; ++kk) {
-                const int j = 8 * b + kk;
-                if (j >= K) break;
-                if (Lh[2 * j + X] < 0x64FFu) x |= 1u << kk;
-            }
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                x |= (((wv[kk] >> sh) & 0xffffu) < 0x64FFu ? 1u : 0u) << kk;
+            const int rest = K - 8 * b;
+            if (rest < 8) x &= (1u << rest) - 1u;
             p.bits[out_row(p, cw[X]) * nbytes + b] = (uint8_t)x;
         }
         if (tid == 0) p.iters[out_row(p, cw[X])] = t[X];
