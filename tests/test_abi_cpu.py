@@ -91,3 +91,41 @@ def test_selftest_rejects_bad_limits_on_host(L):
     L.ldpc_selftest_wait_timeout.argtypes = [ctypes.c_uint, ctypes.c_void_p, ctypes.c_void_p]
     assert L.ldpc_selftest_wait_timeout(0, None, None) == 1
     assert L.ldpc_selftest_wait_timeout((1 << 22) + 1, None, None) == 1
+
+
+def test_work_item_word_layout(L):
+    """The raw-word view of a work-item table (the serving path's) puts each field where
+    the C struct has it: four pointers in words 0..3, then the three ints packed in words 4
+    and 5; the word offsets the serving backend patches are those of hard_bits and iters."""
+    import numpy as np
+
+    import paper_2009_05534_gb300 as pkg
+    assert pkg.WORK_ITEM_WORDS * 8 == ctypes.sizeof(pkg.WorkItem) == pkg.work_item_dtype.itemsize
+    t = np.zeros(3, dtype=pkg.work_item_dtype)
+    t["graph"], t["llr"], t["hard_bits"], t["iters"] = 11, 22, 33, 44
+    t["n_rows"], t["n_tx"], t["max_iter"] = 5, 6, 7
+    w = t.view(np.uint64).reshape(3, pkg.WORK_ITEM_WORDS)
+    assert (w[:, 0] == 11).all() and (w[:, 1] == 22).all()
+    assert (w[:, pkg.WorkItem.hard_bits.offset // 8] == 33).all()
+    assert (w[:, pkg.WorkItem.iters.offset // 8] == 44).all()
+    c = pkg.WorkItem.from_buffer_copy(t[1].tobytes())
+    assert (c.graph, c.llr, c.hard_bits, c.iters) == (11, 22, 33, 44)
+    assert (c.n_rows, c.n_tx, c.max_iter) == (5, 6, 7)
+
+
+def test_host_side_rejections_of_the_serving_entries(L):
+    """Malformed work-item word arrays and row maps are refused on the host, before any
+    library or device call."""
+    import numpy as np
+
+    import paper_2009_05534_gb300 as pkg
+    good = np.zeros((4, pkg.WORK_ITEM_WORDS), np.uint64)
+    for bad in (good.astype(np.int64), good[:, :5].copy(), good[::2], good.reshape(-1)):
+        with pytest.raises(ValueError):
+            pkg.decode_list_words(bad)
+    with pytest.raises(ValueError):
+        pkg.decode_rows_host_maps(None, None, np.zeros(3, np.int32), np.zeros(4, np.int32), 5,
+                                  bits=None, iters=None)
+    with pytest.raises(ValueError):
+        pkg.decode_rows_host_maps(None, None, np.zeros((2, 2), np.int32),
+                                  np.zeros((2, 2), np.int32), 5, bits=None, iters=None)
