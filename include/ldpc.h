@@ -242,7 +242,8 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
  *     counter is cleared by each call.
  *   - The table is uploaded from pageable memory, so the call may wait for the stream's
  *     earlier work before it returns.
- * Outputs and supported shapes are those of ldpc_decode_list. */
+ * Outputs, supported shapes and the kernel choice (opts->threads_per_row) are those of
+ * ldpc_decode_list. */
 ldpc_status ldpc_decode_list_noalloc(const ldpc_work_item *items, int n_items,
                                      ldpc_stream_t stream, const ldpc_decode_opts *opts);
 
