@@ -156,6 +156,55 @@ def test_list_small_lifting_sizes_and_many_items(ldpc):
         g.close()
 
 
+def test_list_llr_rows_at_every_byte_alignment(ldpc):
+    """Items whose LLR rows start at every offset modulo 16 inside one device buffer (the
+    low-latency list kernel stages a row with 16-byte loads of its aligned middle and byte
+    loads of both ragged ends): both list kernels against each other and the oracle."""
+    rng = np.random.default_rng(41)
+    graphs, wls, offs = {}, [], []
+    pos = 0
+    for k in range(32):
+        kind = "BG1" if k % 2 else "BG2"
+        Z = int(rng.choice([6, 32, 96, 384]))
+        rate = Fraction(str(rng.choice(RATES[kind])))
+        wl = make_workload(kind, Z, 1, float(rng.uniform(0.5, 3.0)), rate=rate, seed=900 + k,
+                           graph_seed=0)
+        if (kind, Z) not in graphs:
+            graphs[(kind, Z)] = ldpc.Graph(wl.base, wl.K_b, Z)
+        pos += (k % 16 - pos) % 16                   # row k starts at offset k mod 16
+        offs.append(pos)
+        wls.append(wl)
+        pos += wl.n_tx
+    host = np.zeros(pos + 16, np.int8)
+    qs = []
+    for wl, o in zip(wls, offs):
+        q = wl.llr_int8()
+        host[o:o + wl.n_tx] = q[0]
+        qs.append(q)
+    buf = torch.from_numpy(host).cuda()
+    assert sorted({(buf.data_ptr() + o) % 16 for o in offs}) == list(range(16))
+    outs = {}
+    for tpr in (1, 2):
+        items = []
+        for wl, o in zip(wls, offs):
+            bits = torch.zeros(((wl.K + 7) // 8,), dtype=torch.uint8, device="cuda")
+            it = torch.zeros((1,), dtype=torch.int32, device="cuda")
+            items.append((graphs[(wl.kind, wl.Z)], buf[o:o + wl.n_tx], bits, it, wl.n_rows,
+                          wl.n_tx, 7))
+        ldpc.decode_list(items, early_stop=True, threads_per_row=tpr)
+        torch.cuda.synchronize()
+        outs[tpr] = [(b.cpu().numpy(), int(i.item())) for (_, _, b, i, *_r) in items]
+    for k, (wl, q) in enumerate(zip(wls, qs)):
+        assert np.array_equal(outs[2][k][0], outs[1][k][0]) and outs[2][k][1] == outs[1][k][1]
+        if k % 4 == 0:
+            ref = oracle.decode_layered(wl.base, wl.K_b, wl.Z, wl.n_rows, q, algo=oracle.OFFSET,
+                                        max_iter=7, early_stop=True)
+            assert np.array_equal(ldpc.unpack_bits(outs[2][k][0][None, :], wl.K), ref.bits)
+            assert outs[2][k][1] == int(ref.iters[0])
+    for g in graphs.values():
+        g.close()
+
+
 def test_list_dense_graph_falls_back(ldpc):
     """A graph whose messages do not fit the low-latency kernel's Tensor Memory at two
     threads per row pair (52 rows of degree 19 at Z = 160: 520 slots, two warps per lane
