@@ -219,21 +219,72 @@ def test_fp16_bg1_z64(ldpc):
     assert (np.abs(post.astype(np.float32) - ref.post.astype(np.float32)) <= tol).all()
 
 
-# ------------------------------------------------- full size, sampled against the oracle
+def test_fp16_hand_example(ldpc):
+    """The binary16 decoder on the hand-worked example whose every binary16 rounding
+    (v = L - c, corrected magnitudes, posteriors, ties to even, binary16 parameters, the
+    learned correction's two roundings) changes a value."""
+    g = json.load(open(os.path.join(GOLDEN, "hand_layered_f16_z2.json")))
+    code = g["code"]
+    graph = ldpc.Graph(np.array(code["base"], np.int16), code["K_b"], code["Z"])
+    llr = torch.tensor([g["llr"]], dtype=torch.float16).cuda()
+    ex = g["normalised_0.75"]
+    for T in (1, 2):
+        bits, _, post, c2v = ldpc.decode(graph, llr, T, early_stop=False, punct_cols=0,
+                                         n_rows=code["n_rows"], debug=True,
+                                         algo=ldpc.NORMALISED, alpha=0.75)
+        torch.cuda.synchronize()
+        assert post.cpu().double().numpy()[0].tolist() == ex[f"T{T}"]["post"]
+        assert c2v.cpu().double().numpy()[0].tolist() == ex[f"T{T}"]["c2v"]
+    assert _unpack(ldpc, bits.cpu().numpy(), 4)[0].tolist() == ex["hard_bits_K"]
+    lx = g["learned_T1"]
+    tab = torch.tensor(lx["table"], dtype=torch.float32).cuda()
+    _, _, post, c2v = ldpc.decode(graph, llr, 1, early_stop=False, punct_cols=0,
+                                  n_rows=code["n_rows"], debug=True, algo=ldpc.LEARNED,
+                                  learned=tab)
+    torch.cuda.synchronize()
+    graph.sync_status()
+    assert post.cpu().double().numpy()[0].tolist() == lx["post"]
+    assert c2v.cpu().double().numpy()[0].tolist() == lx["c2v"]
+    graph.close()
 
-def test_int8_full_batch_sampled(ldpc):
-    """Batch 1024, BG1 Z=384, T=10 in the benchmark's launch configuration; 24 sampled
-    codewords are decoded by the oracle one by one and must match bit for bit."""
+
+# ------------------------------------------------------- full size, the whole batch
+
+
+@pytest.fixture(scope="module")
+def headline():
+    """The benchmark's workload: BG1 Z=384, 1024 codewords at 1.5 dB, int8."""
     wl = make_workload("BG1", 384, 1024, 1.5, seed=0)
-    q = wl.llr_int8()
-    bits, iters = _gpu(ldpc, wl, q, 10, early_stop=False, debug=False)
-    gb = _unpack(ldpc, bits, wl.K)
-    rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(1024, 24, replace=False))
-    ref = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q[idx], algo=oracle.OFFSET,
-                                max_iter=10, early_stop=False, threads=8)
-    assert np.array_equal(gb[idx], ref.bits)
-    assert (iters == 10).all()
+    return wl, wl.llr_int8()
+
+
+@pytest.mark.parametrize("early_stop", [False, True])
+def test_int8_full_batch(ldpc, headline, early_stop):
+    """Batch 1024, BG1 Z=384, T=10 in the benchmark's launch configuration (work counter,
+    staging ahead, on-demand claims near the end of the batch, lane refill under the
+    stopping rule): every codeword's hard bits and iteration count equal the oracle's."""
+    wl, q = headline
+    bits, iters = _gpu(ldpc, wl, q, 10, early_stop=early_stop, debug=False)
+    ref = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=10, early_stop=early_stop, threads=16)
+    assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
+    assert np.array_equal(iters, ref.iters)
+    if early_stop:
+        assert 1 <= ref.iters.min() and ref.iters.max() == 10 and ref.iters.mean() < 9
+
+
+def test_int8_full_batch_posteriors(ldpc, headline):
+    """The same batch with the stopping rule and the debug outputs: all 1024 codewords'
+    final posteriors and check-to-variable messages equal the oracle's."""
+    wl, q = headline
+    bits, iters, post, c2v = _gpu(ldpc, wl, q, 10, early_stop=True, threads_per_row=1)
+    ref = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, q, algo=oracle.OFFSET,
+                                max_iter=10, early_stop=True, want_post=True, want_c2v=True,
+                                threads=16)
+    assert np.array_equal(iters, ref.iters)
+    assert np.array_equal(post, ref.post)
+    assert np.array_equal(c2v, ref.c2v)
+    assert np.array_equal(_unpack(ldpc, bits, wl.K), ref.bits)
 
 
 @pytest.mark.parametrize("tpr", [1, 2, 4])

@@ -72,6 +72,38 @@ def test_hand_example_saturation():
     assert r.bits[0].tolist() == ex["hard_bits_K"]
 
 
+def test_hand_example_binary16_z2():
+    """The half-precision decoder (Sec. IV) on hand-worked values where each binary16
+    rounding changes the result: of v = L - c (it2, a tie at 1108.5), of every corrected
+    magnitude (0.75 * 1101 = 825.75), of every posterior (2995.875 -> 2996), ties to even,
+    the correction parameters entering as binary16 (0.7 -> 0.7001953125) and the learned
+    correction rounding m - gamma before the product (258.375 -> 258.5)."""
+    g = _load("hand_layered_f16_z2.json")
+    code = g["code"]
+    base = np.array(code["base"], np.int16)
+    llr = np.array([g["llr"]], np.float16)
+    assert llr[0].astype(np.float64).tolist() == g["llr"]          # inputs are binary16 values
+    ex = g["normalised_0.75"]
+    for T in (1, 2):
+        r = oracle.decode_layered(base, code["K_b"], code["Z"], code["n_rows"], llr,
+                                  algo=oracle.NORMALISED, alpha=0.75, max_iter=T,
+                                  early_stop=False, punct=code["punct"], want_post=True,
+                                  want_c2v=True)
+        assert r.post[0].astype(np.float64).tolist() == ex[f"T{T}"]["post"]
+        assert r.c2v[0].astype(np.float64).tolist() == ex[f"T{T}"]["c2v"]
+    r = oracle.decode_layered(base, code["K_b"], code["Z"], code["n_rows"], llr,
+                              algo=oracle.NORMALISED, alpha=0.75, max_iter=2, early_stop=True,
+                              punct=0)
+    assert r.iters[0] == 2 and r.bits[0].tolist() == ex["hard_bits_K"]
+    lx = g["learned_T1"]
+    r = oracle.decode_layered(base, code["K_b"], code["Z"], code["n_rows"], llr,
+                              algo=oracle.LEARNED, learned=np.array(lx["table"], np.float32),
+                              max_iter=1, early_stop=False, punct=0, want_post=True,
+                              want_c2v=True)
+    assert r.post[0].astype(np.float64).tolist() == lx["post"]
+    assert r.c2v[0].astype(np.float64).tolist() == lx["c2v"]
+
+
 # ------------------------------------------------------------- P3: check-node closed form
 
 def _cn_brute(v, corr):
