@@ -441,6 +441,19 @@ def decode_list_noalloc(items: np.ndarray, *, stream=None, early_stop=True,
            "ldpc_decode_list_noalloc")
 
 
+def state_bytes(n_vars: int, n_edges: int, Z: int, eps: int) -> tuple[int, int]:
+    """Per-codeword decoder state in the storage model of Sec. IV: posteriors
+    S_v = eps * N_c and check-to-variable messages S_c->v = eps * Z * sum_r w_r bytes, for
+    N_c = n_vars posteriors, sum_r w_r = n_edges circulants and eps bytes per value.
+
+    The batch kernels keep both on chip: the int8 decoder holds posteriors as binary16
+    (eps = 2) in shared memory and messages as bytes (eps = 1) in Tensor Memory, the
+    binary16 decoder both at eps = 2."""
+    if min(n_vars, n_edges, Z, eps) < 0:
+        raise ValueError("sizes must be non-negative")
+    return eps * n_vars, eps * Z * n_edges
+
+
 def unpack_bits(packed: np.ndarray, K: int) -> np.ndarray:
     """LSB-first packed hard bits [B][ceil(K/8)] -> uint8 [B][K]."""
     return np.unpackbits(np.asarray(packed, dtype=np.uint8), axis=1, bitorder="little")[:, :K]

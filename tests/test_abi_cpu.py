@@ -129,3 +129,24 @@ def test_host_side_rejections_of_the_serving_entries(L):
     with pytest.raises(ValueError):
         pkg.decode_rows_host_maps(None, None, np.zeros((2, 2), np.int32),
                                   np.zeros((2, 2), np.int32), 5, bits=None, iters=None)
+
+
+def test_storage_model_matches_the_paper():
+    """Sec. IV storage model: the paper's printed S_v and S_c->v for BG1 at Z = 384 (8-bit
+    and 16-bit values) from the per-codeword state the decoders keep on chip."""
+    import json
+
+    import paper_2009_05534_gb300 as pkg
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_storage.json")))
+    Z, n_vars, E = g["Z"], g["N_bg"] * g["Z"], g["E_bg1"]
+    for eps in (1, 2):
+        s_v, s_c = pkg.state_bytes(n_vars, E, Z, eps)
+        # the paper prints whole kB (1000 B), truncated: 121 344 B -> 121, 242 688 B -> 242
+        assert s_v // 1000 == g["S_v_kB"][str(eps)]
+        assert s_c // 1000 == g["S_c2v_kB"][str(eps)]
+    # the int8 batch kernel's layout at the headline graph (E = 323): two codewords'
+    # binary16 posteriors fill 104 448 B of shared memory and their byte messages 248 064 B
+    # of the 256 kB of Tensor Memory
+    s_v, _ = pkg.state_bytes(68 * 384, 323, 384, 2)
+    _, s_c = pkg.state_bytes(68 * 384, 323, 384, 1)
+    assert 2 * s_v == 104448 and 2 * s_c == 248064 <= 256 * 1024

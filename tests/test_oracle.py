@@ -372,6 +372,58 @@ def test_bler_monotone_in_ebn0():
     assert all(bl[i + 1] <= bl[i] for i in range(3)), bl
 
 
+def _bler_cfg2(n_cw=384, grid=tuple(0.5 + 0.25 * k for k in range(9))):
+    """BLER of the BG1-shaped Z=384 rate-1/3 QPSK workload with the stopping rule (T=10):
+    int8 offset-1 at LLR scale 4 and 2, and fp32 normalised (alpha 0.75), same codewords
+    and noise at every Eb/N0."""
+    out = {"i8s4": [], "i8s2": [], "f32": []}
+    for eb in grid:
+        wl = make_workload("BG1", 384, n_cw, float(eb), seed=21)
+        for name, llr, kw in (("i8s4", wl.llr_int8(4.0), dict(algo=oracle.OFFSET, offset_q=1)),
+                              ("i8s2", wl.llr_int8(2.0), dict(algo=oracle.OFFSET, offset_q=1)),
+                              ("f32", wl.llr.astype(np.float32),
+                               dict(algo=oracle.NORMALISED, alpha=0.75))):
+            r = oracle.decode_layered(wl.base, wl.K_b, 384, wl.n_rows, llr, max_iter=10,
+                                      early_stop=True, threads=8, **kw)
+            out[name].append(float((r.bits != wl.info).any(axis=1).mean()))
+    return np.array(grid), {k: np.array(v) for k, v in out.items()}
+
+
+def _crossing(grid, bler, level, n_cw):
+    """Eb/N0 where the BLER curve first falls to `level` (log-linear between grid points;
+    a measured zero counts as half a block error)."""
+    b = np.maximum(bler, 0.5 / n_cw)
+    for k in range(len(grid) - 1):
+        if b[k] > level >= b[k + 1]:
+            t = np.log(b[k] / level) / np.log(b[k] / b[k + 1])
+            return float(grid[k] + t * (grid[k + 1] - grid[k]))
+    raise AssertionError(f"BLER never crosses {level}: {bler}")
+
+
+@pytest.mark.slow
+def test_p5_p6_bg1_z384_rate_one_third():
+    """P5 and P6 on the headline workload (384 codewords per point, 0.5..2.5 dB).
+
+    P5: BLER does not increase with Eb/N0, for fp32 normalised min-sum and for the int8
+    decoder at LLR scale 2.  P6: the int8 decoder reaches BLER 1e-1 within 0.3 dB of fp32
+    normalised, at LLR scale 4 and at scale 2.  At scale 4 (posteriors and messages sharing
+    the 8-bit range) P5 does not hold: posteriors that saturate before the codeword
+    converges leave an error floor of a few percent that does not fall with Eb/N0, while
+    scale 2 decodes every codeword from 1.25 dB on; that measured property of the 8-bit
+    arithmetic is asserted as well."""
+    n = 384
+    grid, b = _bler_cfg2(n)
+    for name in ("f32", "i8s2"):
+        assert all(b[name][k + 1] <= b[name][k] for k in range(len(grid) - 1)), (name, b[name])
+    ref = _crossing(grid, b["f32"], 0.1, n)
+    for name in ("i8s4", "i8s2"):
+        assert abs(_crossing(grid, b[name], 0.1, n) - ref) <= 0.3, (name, b[name], b["f32"])
+    hi = grid >= 1.5
+    assert (b["i8s2"][hi] == 0).all() and (b["f32"][hi] == 0).all()
+    assert b["i8s4"][hi].max() > 0.01, b["i8s4"]                 # an error floor at scale 4
+    assert b["i8s4"][-1] > b["i8s4"][hi].min(), b["i8s4"]       # not monotone at scale 4
+
+
 @pytest.mark.slow
 def test_layered_vs_flooding_iterations():
     """Sec. III: layered needs about half the iterations of flooding.  Layered at T and
