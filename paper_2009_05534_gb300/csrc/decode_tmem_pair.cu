@@ -45,9 +45,11 @@ namespace {
 using namespace h2;
 using namespace tm;
 
-struct EdgeMetaQ {
-    int base;      // c*Z + s
-    int thresh;    // Z - s: rows at or above it wrap
+// Per edge: the circulant's shift and the column's place in the posterior array, both in
+// bytes (copied to shared memory; every thread of a row step reads the same entry).
+struct __align__(8) EdgeMetaQ {
+    int s4;        // 4 * s
+    int col4;      // 4 * c * Z
 };
 
 constexpr int kMaxEdgesQ = 1024;
@@ -60,7 +62,7 @@ struct PairParams {
     int ncols;                   // TMEM columns per thread: ceil(E / 2)
     int use_tma;                 // channel LLRs staged by 1-D bulk copies
     int stage_bytes;             // per-lane staging buffer (multiple of 16)
-    int off_lb, off_stage;       // shared-memory offsets of the posteriors and the staging
+    int off_meta, off_stage;     // shared-memory offsets of the edge table and the staging
     int row[kMaxRowsQ + 1];      // edge offsets of the rows
     EdgeMetaQ meta[kMaxEdgesQ];
 };
@@ -68,21 +70,25 @@ struct PairParams {
 // --------------------------------------------------------------------------- one layer
 
 // Thread i processes check row i (both lanes) of a layer of degree D whose first edge sits
-// in the upper half of its TMEM column when P = 1.
+// in the upper half of its TMEM column when P = 1.  Posterior word (c, j) sits at byte
+// 4 (c Z + j) of shared memory.
 template <int D, int P>
-__device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, uint32_t *Lb, uint32_t tcolumn,
-                                       int e0, int Z, int i, bool store) {
+__device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lbytes,
+                                       uint32_t tcolumn, int e0, uint32_t i4, uint32_t i4z,
+                                       bool store) {
     constexpr int NC = (P + D + 1) / 2;
     uint32_t cm[NC];
     twait_st();
     tload<NC>(tcolumn, cm);
     uint32_t X[D];
-    int addr[D];
+    uint32_t off[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const EdgeMetaQ mt = meta[e0 + j];
-        addr[j] = i + mt.base - (i >= mt.thresh ? Z : 0);
-        X[j] = Lb[addr[j]];
+        // (i + s) mod Z without a compare: i + s - Z is negative (a huge unsigned value)
+        // unless the circulant wraps row i
+        off[j] = min(i4 + (uint32_t)mt.s4, i4z + (uint32_t)mt.s4) + (uint32_t)mt.col4;
+        X[j] = *reinterpret_cast<const uint32_t *>(Lbytes + off[j]);
     }
     twait_ld();
     uint32_t m1 = kInf2, m2 = kInf2;
@@ -98,9 +104,9 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, uint32_t *Lb, uint
         X[j] = x;
     }
     const uint32_t SO = (m1 & kSign2) | kOne2;
-    const uint32_t a1 = m1 & kAbs2, a2 = m2 & kAbs2;
+    const uint32_t a1 = m1 & kAbs2;
     const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);
-    const uint32_t T1 = h2add(h2add(a1, a2), kNegOne2);
+    const uint32_t T1 = h2add(h2add(a1, m2), kNegOne2);       // m2 is never negative
     uint32_t C[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -110,7 +116,7 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, uint32_t *Lb, uint
         C[j] = h2fma(ex, sg, kBias2);                          // c' + 1152
         uint32_t L = h2add(C[j], h2add(x, kP127));             // (x + c') + 1279
         L = h2max(h2min(L, kPostHi), kPostLo);
-        if (store) Lb[addr[j]] = L;
+        if (store) *reinterpret_cast<uint32_t *>(Lbytes + off[j]) = L;
     }
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
@@ -127,20 +133,22 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, uint32_t *Lb, uint
 }
 
 template <int D>
-__device__ __forceinline__ void pq_row_any(const EdgeMetaQ *meta, uint32_t *Lb, uint32_t tbase,
-                                           int e0, int Z, int i, bool store) {
+__device__ __forceinline__ void pq_row_any(const EdgeMetaQ *meta, unsigned char *Lbytes,
+                                           uint32_t tbase, int e0, uint32_t i4, uint32_t i4z,
+                                           bool store) {
     if (e0 & 1)
-        pq_row<D, 1>(meta, Lb, tbase + (uint32_t)(e0 >> 1), e0, Z, i, store);
+        pq_row<D, 1>(meta, Lbytes, tbase + (uint32_t)(e0 >> 1), e0, i4, i4z, store);
     else
-        pq_row<D, 0>(meta, Lb, tbase + (uint32_t)(e0 >> 1), e0, Z, i, store);
+        pq_row<D, 0>(meta, Lbytes, tbase + (uint32_t)(e0 >> 1), e0, i4, i4z, store);
 }
 
-__device__ __forceinline__ void pq_dispatch(int d, const EdgeMetaQ *meta, uint32_t *Lb,
-                                            uint32_t tbase, int e0, int Z, int i, bool store) {
+__device__ __forceinline__ void pq_dispatch(int d, const EdgeMetaQ *meta, unsigned char *Lbytes,
+                                            uint32_t tbase, int e0, uint32_t i4, uint32_t i4z,
+                                            bool store) {
     switch (d) {
 #define LDPC_PQ_CASE(D) \
     case D:             \
-        pq_row_any<D>(meta, Lb, tbase, e0, Z, i, store); \
+        pq_row_any<D>(meta, Lbytes, tbase, e0, i4, i4z, store); \
         break;
         LDPC_PQ_CASE(2) LDPC_PQ_CASE(3) LDPC_PQ_CASE(4) LDPC_PQ_CASE(5) LDPC_PQ_CASE(6)
         LDPC_PQ_CASE(7) LDPC_PQ_CASE(8) LDPC_PQ_CASE(9) LDPC_PQ_CASE(10) LDPC_PQ_CASE(11)
@@ -154,12 +162,14 @@ __device__ __forceinline__ void pq_dispatch(int d, const EdgeMetaQ *meta, uint32
 
 // parity masks of check row i over a row's edges: 0xFFFF in a lane whose codeword has an
 // odd number of negative posteriors on the row
-__device__ __forceinline__ uint32_t pq_parity(const EdgeMetaQ *meta, const uint32_t *Lb, int e0,
-                                              int d, int Z, int i) {
+__device__ __forceinline__ uint32_t pq_parity(const EdgeMetaQ *meta, const unsigned char *Lbytes,
+                                              int e0, int d, uint32_t i4, uint32_t i4z) {
     uint32_t par = 0;
     for (int j = 0; j < d; ++j) {
         const EdgeMetaQ mt = meta[e0 + j];
-        par ^= h2lt_mask(Lb[i + mt.base - (i >= mt.thresh ? Z : 0)], kPostBias);
+        const uint32_t off =
+            min(i4 + (uint32_t)mt.s4, i4z + (uint32_t)mt.s4) + (uint32_t)mt.col4;
+        par ^= h2lt_mask(*reinterpret_cast<const uint32_t *>(Lbytes + off), kPostBias);
     }
     return par;
 }
@@ -176,10 +186,12 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
     const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x;
     const bool store = tid < Z;
     const int i = store ? tid : Z - 1;                // spare threads shadow the last row
-    // shared memory: edge metadata | posterior words | two LLR staging buffers
-    EdgeMetaQ *s_meta = reinterpret_cast<EdgeMetaQ *>(smem);
-    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem + pp.off_lb);
-    uint16_t *Lh = reinterpret_cast<uint16_t *>(smem + pp.off_lb);   // lane X of word j: Lh[2j + X]
+    const uint32_t i4 = 4u * (uint32_t)i, i4z = 4u * (uint32_t)(i - Z);
+    // shared memory: posterior words (from offset 0) | edge table | two LLR staging buffers
+    EdgeMetaQ *s_meta = reinterpret_cast<EdgeMetaQ *>(smem + pp.off_meta);
+    unsigned char *Lbytes = smem;
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem);
+    uint16_t *Lh = reinterpret_cast<uint16_t *>(smem);   // lane X of word j: Lh[2j + X]
     int8_t *stage = reinterpret_cast<int8_t *>(smem + pp.off_stage);
 
     for (int e = tid; e < E; e += nthr) s_meta[e] = pp.meta[e];
@@ -341,7 +353,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
 #pragma unroll 1
         for (int r = 0; r < n_rows; ++r) {
             const int e0 = pp.row[r];
-            pq_dispatch(pp.row[r + 1] - e0, s_meta, Lb, tbase, e0, Z, i, store);
+            pq_dispatch(pp.row[r + 1] - e0, s_meta, Lbytes, tbase, e0, i4, i4z, store);
             named_sync(1, nthr);
         }
         ++t[0];
@@ -368,7 +380,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
                 }
                 if ((wacc | *vbad) == 0xFFFFFFFFu) break;
                 const int e0 = pp.row[r];
-                acc |= pq_parity(s_meta, Lb, e0, pp.row[r + 1] - e0, Z, i);
+                acc |= pq_parity(s_meta, Lbytes, e0, pp.row[r + 1] - e0, i4, i4z);
             }
             const uint32_t wacc = __reduce_or_sync(0xffffffffu, acc);
             if ((tid & 31) == 0 && wacc != seen) atomicOr(&s_bad[sb], wacc);
@@ -430,12 +442,13 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
     if (warp == 0) tmem_dealloc(s_tmem_base, kTmemColsQ);
 }
 
-size_t pair_smem_bytes(const DecodeParams &p, bool tma, int *off_lb, int *off_stage,
+size_t pair_smem_bytes(const DecodeParams &p, bool tma, int *off_meta, int *off_stage,
                        int *stage_bytes) {
-    const int lb = (int)(((size_t)p.E * sizeof(EdgeMetaQ) + 15) & ~(size_t)15);
-    const int st = (int)((lb + (size_t)p.n_cols * p.Z * 4 + 15) & ~(size_t)15);
+    const size_t lb = (size_t)p.n_cols * p.Z * 4;
+    const int mt = (int)((lb + 15) & ~(size_t)15);
+    const int st = (int)((mt + (size_t)p.E * sizeof(EdgeMetaQ) + 15) & ~(size_t)15);
     const int sb = tma ? ((p.n_tx + 15) & ~15) : 0;
-    if (off_lb) *off_lb = lb;
+    if (off_meta) *off_meta = mt;
     if (off_stage) *off_stage = st;
     if (stage_bytes) *stage_bytes = sb;
     return (size_t)st + 2 * (size_t)sb;
@@ -460,9 +473,8 @@ ldpc_status launch_pair(const DecodeParams &p, cudaStream_t stream) {
     pp.ncols = (p.E + 1) / 2;
     for (int e = 0; e < p.E; ++e) {
         const uint32_t ed = p.h_edges[e];
-        const int c = (int)(ed >> 16), s = (int)(ed & 0xffffu);
-        pp.meta[e].base = c * p.Z + s;
-        pp.meta[e].thresh = p.Z - s;
+        pp.meta[e].s4 = 4 * (int)(ed & 0xffffu);
+        pp.meta[e].col4 = 4 * (int)(ed >> 16) * p.Z;
     }
     // bulk copies need 16-byte aligned rows; at least 120 kB of shared memory so that one
     // block occupies the SM (its TMEM allocation takes all 512 columns)
@@ -470,7 +482,7 @@ ldpc_status launch_pair(const DecodeParams &p, cudaStream_t stream) {
                   p.n_tx > 0 && p.n_tx < (1 << 20))
                      ? 1
                      : 0;
-    size_t smem = pair_smem_bytes(p, pp.use_tma != 0, &pp.off_lb, &pp.off_stage, &pp.stage_bytes);
+    size_t smem = pair_smem_bytes(p, pp.use_tma != 0, &pp.off_meta, &pp.off_stage, &pp.stage_bytes);
     if (smem < 120 * 1024) smem = 120 * 1024;
     int dev = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LDPC_ERR_CUDA;
