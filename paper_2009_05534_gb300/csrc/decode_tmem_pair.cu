@@ -71,11 +71,12 @@ struct PairParams {
 
 // Thread i processes check row i (both lanes) of a layer of degree D whose first edge sits
 // in the upper half of its TMEM column when P = 1.  Posterior word (c, j) sits at byte
-// 4 (c Z + j) of shared memory.
+// 4 (c Z + j) of shared memory.  The row waits at the layer barrier (nthr threads) after
+// loading its own messages and computing its addresses.
 template <int D, int P>
 __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lbytes,
                                        uint32_t tcolumn, int e0, uint32_t i4, uint32_t i4z,
-                                       bool store) {
+                                       bool store, int nthr) {
     constexpr int NC = (P + D + 1) / 2;
     uint32_t cm[NC];
     twait_st();
@@ -88,8 +89,12 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
         // (i + s) mod Z without a compare: i + s - Z is negative (a huge unsigned value)
         // unless the circulant wraps row i
         off[j] = min(i4 + (uint32_t)mt.s4, i4z + (uint32_t)mt.s4) + (uint32_t)mt.col4;
-        X[j] = *reinterpret_cast<const uint32_t *>(Lbytes + off[j]);
     }
+    // the layer barrier: the previous layer's posterior stores are visible after it; the
+    // dispatch to this row's code, its messages and its addresses are ready before it
+    named_sync(1, nthr);
+#pragma unroll
+    for (int j = 0; j < D; ++j) X[j] = *reinterpret_cast<const uint32_t *>(Lbytes + off[j]);
     twait_ld();
     uint32_t m1 = kInf2, m2 = kInf2;
 #pragma unroll
@@ -132,23 +137,19 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
     tstore<NC>(tcolumn, cm);
 }
 
-template <int D>
-__device__ __forceinline__ void pq_row_any(const EdgeMetaQ *meta, unsigned char *Lbytes,
-                                           uint32_t tbase, int e0, uint32_t i4, uint32_t i4z,
-                                           bool store) {
-    if (e0 & 1)
-        pq_row<D, 1>(meta, Lbytes, tbase + (uint32_t)(e0 >> 1), e0, i4, i4z, store);
-    else
-        pq_row<D, 0>(meta, Lbytes, tbase + (uint32_t)(e0 >> 1), e0, i4, i4z, store);
-}
-
-__device__ __forceinline__ void pq_dispatch(int d, const EdgeMetaQ *meta, unsigned char *Lbytes,
+// One dispatch per row on key = 2 D + P (the row's degree and the parity of its first
+// edge), computed a row ahead; the branch happens before the row's layer barrier.
+__device__ __forceinline__ void pq_dispatch(int key, const EdgeMetaQ *meta, unsigned char *Lbytes,
                                             uint32_t tbase, int e0, uint32_t i4, uint32_t i4z,
-                                            bool store) {
-    switch (d) {
-#define LDPC_PQ_CASE(D) \
-    case D:             \
-        pq_row_any<D>(meta, Lbytes, tbase, e0, i4, i4z, store); \
+                                            bool store, int nthr) {
+    const uint32_t tc = tbase + (uint32_t)(e0 >> 1);
+    switch (key) {
+#define LDPC_PQ_CASE(D)                                                   \
+    case 2 * D:                                                           \
+        pq_row<D, 0>(meta, Lbytes, tc, e0, i4, i4z, store, nthr);         \
+        break;                                                            \
+    case 2 * D + 1:                                                       \
+        pq_row<D, 1>(meta, Lbytes, tc, e0, i4, i4z, store, nthr);         \
         break;
         LDPC_PQ_CASE(2) LDPC_PQ_CASE(3) LDPC_PQ_CASE(4) LDPC_PQ_CASE(5) LDPC_PQ_CASE(6)
         LDPC_PQ_CASE(7) LDPC_PQ_CASE(8) LDPC_PQ_CASE(9) LDPC_PQ_CASE(10) LDPC_PQ_CASE(11)
@@ -194,7 +195,13 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
     uint16_t *Lh = reinterpret_cast<uint16_t *>(smem);   // lane X of word j: Lh[2j + X]
     int8_t *stage = reinterpret_cast<int8_t *>(smem + pp.off_stage);
 
+    // per row: first edge and dispatch key 2 D + P (one entry past the last row, unused)
+    __shared__ int s_row[kMaxRowsQ + 1], s_key[kMaxRowsQ + 1];
     for (int e = tid; e < E; e += nthr) s_meta[e] = pp.meta[e];
+    for (int r = tid; r <= n_rows; r += nthr) {
+        s_row[r] = pp.row[r];
+        s_key[r] = r < n_rows ? 2 * (pp.row[r + 1] - pp.row[r]) + (pp.row[r] & 1) : 0;
+    }
     if (tid == 0) {
         if (pp.use_tma) {
             mbar_init(&s_bar[0]);
@@ -350,12 +357,15 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
     int r_scan = 0;                                  // first layer of this warp's next scan
 #pragma unroll 1
     while (!failed && (cw[0] >= 0 || cw[1] >= 0)) {
+        int e0 = s_row[0], key = s_key[0];
 #pragma unroll 1
         for (int r = 0; r < n_rows; ++r) {
-            const int e0 = pp.row[r];
-            pq_dispatch(pp.row[r + 1] - e0, s_meta, Lbytes, tbase, e0, i4, i4z, store);
-            named_sync(1, nthr);
+            const int e0r = e0, keyr = key;
+            e0 = s_row[r + 1];                       // the next row's, read before the barrier
+            key = s_key[r + 1];
+            pq_dispatch(keyr, s_meta, Lbytes, tbase, e0r, i4, i4z, store, nthr);
         }
+        named_sync(1, nthr);                         // the iteration's last layer is done
         ++t[0];
         ++t[1];
         // a5: the stopping rule per lane (bits 0..15: lane 0, 16..31: lane 1); a lane with
