@@ -417,9 +417,10 @@ def latency_measure(wl, graph, reps: int = 50):
 
 # ------------------------------------------------------------------- high load (R = 8/9)
 
-# Eb/N0 per modulation where the int8 decoder's BLER at a 10-iteration cap sits near 1e-2
-# on the BG1-shaped graph at rate 8/9 (oracle sweep, 200 codewords per point)
-HIGH_LOAD = (("16QAM", 7.75), ("64QAM", 11.75))
+# Eb/N0 grids per modulation that carry every decoder and cap through BLER 1e-1 .. 1e-3 on
+# the BG1-shaped graph at rate 8/9 (set from an oracle sweep of 256 codewords per point)
+HIGH_LOAD = (("16QAM", [6.875 + 0.125 * k for k in range(15)]),
+             ("64QAM", [10.875 + 0.125 * k for k in range(15)]))
 
 
 def _timed(fn, reps: int, stream):
@@ -433,52 +434,100 @@ def _timed(fn, reps: int, stream):
     return s.elapsed_time(e) / 1e3 / reps
 
 
-def high_load_measure(batch: int = 8192, caps=(5, 10, 20), reps: int = 5, seed: int = 2):
-    """BG1-shaped Z=384 at rate 8/9 (5 rows), 16QAM / 64QAM max-log LLRs, batch 8192,
-    iteration caps 5/10/20 with early stop: int8 (offset 1) and binary16 (normalised 0.75)
-    message storage side by side.  Inputs rotate over device copies larger than L2."""
+def _crossings(ebn0s, blers, levels=(1e-1, 1e-2, 1e-3)):
+    """Eb/N0 where a BLER curve first falls to each level (log-linear between points, a
+    zero counting as below every level), None where it never does."""
+    out = {}
+    for lv in levels:
+        at = None
+        for k in range(len(ebn0s) - 1):
+            b0, b1 = blers[k], blers[k + 1]
+            if b0 > lv >= b1:
+                if b1 <= 0.0:
+                    at = ebn0s[k + 1]
+                else:
+                    t = math.log(b0 / lv) / math.log(b0 / b1)
+                    at = ebn0s[k] + t * (ebn0s[k + 1] - ebn0s[k])
+                break
+        if at is None and blers and blers[0] <= lv:
+            at = ebn0s[0]
+        out[f"{lv:g}"] = at
+    return out
+
+
+def high_load_measure(batch: int = 8192, caps=(5, 10, 20), reps: int = 3, seed: int = 2,
+                      alu_peak: float | None = None):
+    """BG1-shaped Z=384 at rate 8/9 (5 rows, N_tx = 9504), 16QAM / 64QAM max-log LLRs,
+    batch 8192, iteration caps 5/10/20 with early stop: int8 (offset 1, LLR scale 4, the
+    headline quantiser), int8 at LLR scale 2 and binary16 (normalised 0.75) message storage
+    side by side, over an Eb/N0 grid per modulation (the same codewords and noise at every
+    point).  Per point: Gbit/s, BLER, mean iterations; per decoder and cap: the Eb/N0 where
+    BLER reaches 1e-1, 1e-2 and 1e-3; and the ALU roofline fraction of the int8 and
+    binary16 decodes (executed edge updates over the int8x4 or fp16x2 issue peak).  Inputs
+    rotate over device copies larger than L2."""
     from fractions import Fraction
 
+    import numpy as np
     import torch
 
     import paper_2009_05534_gb300 as ldpc
     from synth import make_workload
+    from synth.channel import modulate_llr_sweep, quantize_int8, to_fp16
     stream = torch.cuda.Stream()
-    out = []
-    for mod, eb in HIGH_LOAD:
-        wl = make_workload("BG1", 384, batch, eb, rate=Fraction(8, 9), modulation=mod,
+    points, summary = [], []
+    decoders = (("int8", 4.0, dict(algo=ldpc.OFFSET)), ("int8_scale2", 2.0, dict(algo=ldpc.OFFSET)),
+                ("fp16", None, dict(algo=ldpc.NORMALISED, alpha=0.75)))
+    for mod, grid in HIGH_LOAD:
+        wl = make_workload("BG1", 384, batch, grid[0], rate=Fraction(8, 9), modulation=mod,
                            seed=seed, graph_seed=0)
+        E = int((wl.base[:wl.n_rows] >= 0).sum())
         g = ldpc.Graph(wl.base, wl.K_b, 384)
         info = torch.from_numpy(wl.info).cuda()
-        for dtype, host, kw in (("int8", wl.llr_int8(), dict(algo=ldpc.OFFSET)),
-                                ("fp16", wl.llr_fp16(),
-                                 dict(algo=ldpc.NORMALISED, alpha=0.75))):
-            n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
-            with torch.cuda.stream(stream):
-                bufs = [torch.from_numpy(host).cuda() for _ in range(n_copies)]
-            torch.cuda.synchronize()
-            for T in caps:
-                bits = iters = None
+        tx = wl.codewords[:, wl.punct_cols * 384: wl.punct_cols * 384 + wl.n_tx]
+        curve = {(name, T): [] for name, _, _ in decoders for T in caps}
+        for eb, llr in zip(grid, modulate_llr_sweep(tx, grid, wl.meta["rate"], mod, seed)):
+            for name, scale, kw in decoders:
+                host = quantize_int8(llr, scale) if scale else to_fp16(llr)
+                n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
+                with torch.cuda.stream(stream):
+                    b0 = torch.from_numpy(host).cuda()
+                    bufs = [b0] + [b0.clone() for _ in range(n_copies - 1)]
+                torch.cuda.synchronize()
+                for T in caps:
+                    bits = iters = None
 
-                def run(k):
-                    nonlocal bits, iters
-                    bits, iters = ldpc.decode(g, bufs[k % n_copies], T, n_rows=wl.n_rows,
-                                              n_tx=wl.n_tx, early_stop=True, stream=stream,
-                                              **kw)
+                    def run(k):
+                        nonlocal bits, iters
+                        bits, iters = ldpc.decode(g, bufs[k % n_copies], T, n_rows=wl.n_rows,
+                                                  n_tx=wl.n_tx, early_stop=True, stream=stream,
+                                                  **kw)
 
-                for k in range(2):
-                    run(k)
-                sec = _timed(run, reps, stream)
-                got = ldpc.unpack_bits(bits.cpu().numpy(), wl.K)
-                bler = float((torch.from_numpy(got).cuda() != info).any(1).float().mean())
-                out.append({"modulation": mod, "ebn0_db": eb, "max_iter": T, "dtype": dtype,
-                            "gbps": batch * wl.K / sec / 1e9, "bler": bler,
-                            "mean_iterations": float(iters.float().mean())})
-            del bufs
+                    for k in range(2):
+                        run(k)
+                    sec = _timed(run, reps, stream)
+                    got = torch.from_numpy(ldpc.unpack_bits(bits.cpu().numpy(), wl.K)).cuda()
+                    bler = float((got != info).any(1).float().mean())
+                    mit = float(iters.float().mean())
+                    pt = {"modulation": mod, "ebn0_db": eb, "max_iter": T, "dtype": name,
+                          "gbps": batch * wl.K / sec / 1e9, "bler": bler,
+                          "mean_iterations": mit}
+                    if alu_peak:
+                        # executed edge updates / s over the issue peak of the lane format
+                        peak = alu_peak if name.startswith("int8") else alu_peak / 2
+                        pt["roofline_frac"] = mit * E * 384 * batch / sec / peak
+                    points.append(pt)
+                    curve[(name, T)].append(bler)
+                del bufs
+        for (name, T), bl in curve.items():
+            summary.append({"modulation": mod, "dtype": name, "max_iter": T,
+                            "ebn0_db_at_bler": _crossings(grid, bl)})
         g.close()
     return {"workload": "BG1-shaped Z=384 K=8448 R=8/9 (5 rows, N_tx=9504), batch "
-                        f"{batch}, early stop, inputs rotate over copies > L2",
-            "points": out}
+                        f"{batch}, early stop, inputs rotate over copies > L2; int8 = LLR "
+                        "scale 4 (the headline quantiser), int8_scale2 = LLR scale 2; "
+                        "roofline_frac: executed edge updates over the int8x4 (int8) or "
+                        "fp16x2 (binary16) issue peak",
+            "points": points, "bler_crossings": summary}
 
 
 # ------------------------------------------------------------ flooding baseline (Sec. V)
@@ -542,8 +591,9 @@ def learned_measure(table_file: str = LEARNED_TABLE, kind: str = "BG2", Z: int =
                     reps: int = 5):
     """A trained (beta, gamma) table against plain normalised min-sum (alpha 0.75) on the
     same fresh codewords: BLER per Eb/N0 at T = 10 (binary16 LLRs and messages), the Eb/N0
-    of BLER 1e-2 for each, and decode throughput of both at T = 10 and, with early stop,
-    at the plain decoder's BLER-1e-2 point."""
+    of BLER 1e-2 for each, decode throughput of both at T = 10 and, with early stop, at the
+    plain decoder's BLER-1e-2 point, and each decoder with early stop at its own BLER-1e-2
+    point (Gbit/s at equal BLER)."""
     import torch
 
     import paper_2009_05534_gb300 as ldpc
@@ -563,35 +613,51 @@ def learned_measure(table_file: str = LEARNED_TABLE, kind: str = "BG2", Z: int =
     at = {k: ebn0_at(list(grid), v, 1e-2) for k, v in curves.items()}
     eb_op = at["plain"] if at["plain"] is not None else grid[-1]
     stream = torch.cuda.Stream()
-    thr = {}
-    wl = make_workload(kind, Z, batch, float(eb_op), seed=78_000, graph_seed=0)
-    host = wl.llr_fp16()
-    n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
-    with torch.cuda.stream(stream):
-        bufs = [torch.from_numpy(host).cuda() for _ in range(n_copies)]
-    torch.cuda.synchronize()
-    for es in (False, True):
-        for name, kw in (("plain", dict(algo=ldpc.NORMALISED, alpha=0.75)),
-                         ("learned", dict(algo=ldpc.LEARNED, learned=tab))):
-            iters = None
+    kws = {"plain": dict(algo=ldpc.NORMALISED, alpha=0.75),
+           "learned": dict(algo=ldpc.LEARNED, learned=tab)}
 
-            def run(k):
-                nonlocal iters
-                _, iters = ldpc.decode(g, bufs[k % n_copies], T, early_stop=es, stream=stream,
-                                       **kw)
+    def throughput(eb, names, early_stops, seed):
+        """Gbit/s and mean iterations of each decoder on `batch` fresh codewords at eb."""
+        wl = make_workload(kind, Z, batch, float(eb), seed=seed, graph_seed=0)
+        host = wl.llr_fp16()
+        n_copies = max(2, math.ceil(2.2 * L2_BYTES / host.nbytes))
+        with torch.cuda.stream(stream):
+            b0 = torch.from_numpy(host).cuda()
+            bufs = [b0] + [b0.clone() for _ in range(n_copies - 1)]
+        torch.cuda.synchronize()
+        res = {}
+        for es in early_stops:
+            for name in names:
+                out = {}
 
-            for k in range(2):
-                run(k)
-            sec = _timed(run, reps, stream)
-            thr[f"{name}{'_early_stop' if es else ''}"] = {
-                "gbps": batch * wl.K / sec / 1e9, "mean_iterations": float(iters.float().mean())}
-    del bufs
-    g.close()
+                def run(k):
+                    out["o"] = ldpc.decode(g, bufs[k % n_copies], T, early_stop=es,
+                                           stream=stream, **kws[name])
+
+                for k in range(2):
+                    run(k)
+                sec = _timed(run, reps, stream)
+                got = ldpc.unpack_bits(out["o"][0].cpu().numpy(), wl.K)
+                res[f"{name}{'_early_stop' if es else ''}"] = {
+                    "gbps": batch * wl.K / sec / 1e9,
+                    "mean_iterations": float(out["o"][1].float().mean()),
+                    "bler": float((got != wl.info).any(1).mean())}
+        return res
+
+    # both decoders at the plain decoder's BLER-1e-2 point, fixed T and with early stop
+    thr = throughput(eb_op, ("plain", "learned"), (False, True), 78_000)
+    # equal BLER: each decoder with early stop at its own BLER-1e-2 Eb/N0
+    equal = {}
+    for name in ("plain", "learned"):
+        if at[name] is not None:
+            r = throughput(at[name], (name,), (True,), 79_000)[f"{name}_early_stop"]
+            equal[name] = {"ebn0_db": at[name], **r}
     return {"workload": meta.get("code"), "T": T, "llr": "binary16", "eval_codewords": n_cw,
             "ebn0_db": list(grid), "bler_plain": curves["plain"],
             "bler_learned": curves["learned"], "ebn0_at_bler_1e-2": at,
             "gain_db": (at["plain"] - at["learned"]) if None not in at.values() else None,
             "throughput_ebn0_db": eb_op, "throughput_batch": batch, "throughput": thr,
+            "equal_bler_1e-2_early_stop": equal,
             "training": {k: meta["training"].get(k) for k in
                          ("codewords", "epochs", "steps", "lr", "ebn0_db", "loss", "gradient")}}
 
@@ -763,7 +829,7 @@ def run_ours(args):
     latency = latency_measure(wl, graph) if aux and args.latency else None
     bler_curve = bler_curve_measure(graph) if aux and args.bler_curve else None
     flooding = flooding_measure(wl, graph, bufs[0]) if aux and args.flooding else None
-    high_load = high_load_measure() if aux and args.high_load else None
+    high_load = high_load_measure(alu_peak=alu_peak) if aux and args.high_load else None
     learned = learned_bg1 = None
     if aux and args.learned:
         learned = learned_measure()

@@ -79,7 +79,8 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
                                        bool store, int nthr) {
     constexpr int NC = (P + D + 1) / 2;
     uint32_t cm[NC];
-    twait_st();
+    // a row that starts mid-column reads the column the previous row has just stored
+    if constexpr (P == 1) twait_st();
     tload<NC>(tcolumn, cm);
     uint32_t X[D];
     uint32_t off[D];
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
 #pragma unroll 1
     while (!failed && (cw[0] >= 0 || cw[1] >= 0)) {
         int e0 = s_row[0], key = s_key[0];
+        twait_st();                                  // rows starting on a column do not wait
 #pragma unroll 1
         for (int r = 0; r < n_rows; ++r) {
             const int e0r = e0, keyr = key;

@@ -134,14 +134,34 @@ def pam_map(groups: np.ndarray, mh: int) -> np.ndarray:
     return pts[inv[code]]
 
 
-def pam_maxlog_llr(y: np.ndarray, mh: int, n0: float) -> np.ndarray:
-    """Max-log bit LLRs [..][mh] of received per-dimension values y [..]."""
+def _pam_maxlog(y: np.ndarray, mh: int, n0) -> np.ndarray:
     pts, labels = pam_points(mh)
     d2 = (y[..., None] - pts) ** 2
     out = np.empty(y.shape + (mh,), dtype=np.float64)
     for k in range(mh):
         is1 = labels[:, k] == 1
         out[..., k] = (d2[..., is1].min(axis=-1) - d2[..., ~is1].min(axis=-1)) / n0
+    return out
+
+
+def pam_maxlog_llr(y: np.ndarray, mh: int, n0) -> np.ndarray:
+    """Max-log bit LLRs [..][mh] of received per-dimension values y [B][..] (n0 a scalar or
+    [B][1]).  Large inputs are split over rows on a thread pool (element-wise, so the result
+    does not depend on the split)."""
+    workers = min(os.cpu_count() or 1, 16)
+    B = y.shape[0] if y.ndim else 1
+    if workers < 2 or y.ndim < 2 or B < 2 * workers or y.size < (1 << 20):
+        return _pam_maxlog(y, mh, n0)
+    out = np.empty(y.shape + (mh,), dtype=np.float64)
+    cuts = np.linspace(0, B, workers + 1).astype(int)
+    n0a = np.asarray(n0, dtype=np.float64)
+
+    def part(i):
+        lo, hi = int(cuts[i]), int(cuts[i + 1])
+        out[lo:hi] = _pam_maxlog(y[lo:hi], mh, n0a[lo:hi] if n0a.ndim else n0a)
+
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(part, range(workers)))
     return out
 
 
@@ -181,6 +201,35 @@ def modulate_llr(bits: np.ndarray, ebn0_db, rate: float, modulation: str,
     y = x + sigma * std_normals(seed, B, nsym_dims, first_cw)
     llr = pam_maxlog_llr(y, mh, n0)
     return llr.reshape(B, nsym_dims * mh)[:, :n].astype(np.float32)
+
+
+def modulate_llr_sweep(bits: np.ndarray, ebn0s, rate: float, modulation: str, seed: int,
+                       first_cw: int = 0):
+    """Channel LLRs of the same transmitted bits at each Eb/N0 in `ebn0s` (a generator of
+    float32 [B][n] arrays): the symbols and the standard normals are computed once, and each
+    array equals modulate_llr(bits, e, rate, modulation, seed, first_cw)."""
+    B, n = bits.shape
+    m = _BITS_PER_SYMBOL.get(modulation)
+    if m is None:
+        raise ValueError(f"unknown modulation {modulation}")
+    if m <= 2:
+        A = 1.0 if m == 1 else 1.0 / math.sqrt(2.0)
+        x = A * (1.0 - 2.0 * bits.astype(np.float64))
+        z = std_normals(seed, B, n, first_cw)
+        for e in ebn0s:
+            n0 = noise_n0(float(e), rate, m)
+            yield (4.0 * A * (x + math.sqrt(n0 / 2.0) * z) / n0).astype(np.float32)
+        return
+    mh = m // 2
+    nsym_dims = (n + mh - 1) // mh
+    pad = nsym_dims * mh - n
+    bp = np.concatenate([bits, np.zeros((B, pad), dtype=bits.dtype)], axis=1)
+    x = pam_map(bp.reshape(B, nsym_dims, mh), mh)
+    z = std_normals(seed, B, nsym_dims, first_cw)
+    for e in ebn0s:
+        n0 = noise_n0(float(e), rate, m)
+        llr = pam_maxlog_llr(x + math.sqrt(n0 / 2.0) * z, mh, n0)
+        yield llr.reshape(B, nsym_dims * mh)[:, :n].astype(np.float32)
 
 
 def quantize_int8(llr: np.ndarray, scale: float = 4.0) -> np.ndarray:

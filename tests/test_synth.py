@@ -219,3 +219,26 @@ def test_threaded_normals_match_single_range():
     a = std_normals(11, 700, 6001, first_cw=5)          # large enough to take the pool
     assert np.array_equal(a, _std_normals(11, 700, 6001, 5))
     assert np.array_equal(a[123], _std_normals(11, 1, 6001, 5 + 123)[0])
+
+
+@pytest.mark.parametrize("mod", ["QPSK", "16QAM", "64QAM"])
+def test_llr_sweep_equals_one_point_at_a_time(mod):
+    """The Eb/N0 sweep helper reuses symbols and normals; each of its LLR arrays equals the
+    single-point channel, also when the max-log demapper splits rows over threads."""
+    from fractions import Fraction
+
+    from synth.channel import modulate_llr, modulate_llr_sweep
+    wl = make_workload("BG1", 64, 300, 3.0, rate=Fraction(2, 3), modulation=mod, seed=4)
+    tx = wl.codewords[:, wl.punct_cols * 64: wl.punct_cols * 64 + wl.n_tx]
+    grid = [2.5, 3.0, 4.25]
+    for e, got in zip(grid, modulate_llr_sweep(tx, grid, wl.meta["rate"], mod, 4)):
+        assert np.array_equal(got, modulate_llr(tx, e, wl.meta["rate"], mod, 4))
+    assert np.array_equal(
+        next(modulate_llr_sweep(tx, [3.0], wl.meta["rate"], mod, 4)), wl.llr)
+
+
+def test_threaded_maxlog_equals_serial():
+    from synth.channel import _pam_maxlog, pam_maxlog_llr
+    y = np.random.default_rng(3).normal(size=(256, 5000))
+    for mh in (2, 3):
+        assert np.array_equal(pam_maxlog_llr(y, mh, 0.37), _pam_maxlog(y, mh, 0.37))
