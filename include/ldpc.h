@@ -340,6 +340,11 @@ const char *ldpc_status_string(ldpc_status s);
 /* Number of kernels this library has launched since it was loaded (all threads). */
 uint64_t ldpc_launch_count(void);
 
+/* Device and pinned-host allocations the library has made since it was loaded (graph
+ * tables, per-stream workspaces, staging buffers), all threads.  Monotone; a
+ * diagnostic. */
+uint64_t ldpc_alloc_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,7 +55,7 @@ ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_dest
                "ldpc_learned_workspace_floats", "ldpc_learned_forward", "ldpc_learned_backward",
                "ldpc_learned_forward_iter", "ldpc_learned_backward_iter",
                "ldpc_flooding_workspace_floats", "ldpc_decode_flooding", "ldpc_decode_rows",
-               "ldpc_decode_rows_host_maps", "ldpc_selftest_wait_timeout")
+               "ldpc_decode_rows_host_maps", "ldpc_selftest_wait_timeout", "ldpc_alloc_count")
 
 
 def lib():
@@ -101,6 +101,8 @@ def lib():
             L.ldpc_status_string.restype = ctypes.c_char_p
             L.ldpc_launch_count.argtypes = []
             L.ldpc_launch_count.restype = ctypes.c_uint64
+            L.ldpc_alloc_count.argtypes = []
+            L.ldpc_alloc_count.restype = ctypes.c_uint64
             L.ldpc_decode_rows.argtypes = [P, P, P, P, i, i, P, ctypes.POINTER(DecodeOpts),
                                            P, P]
             L.ldpc_decode_rows.restype = i
@@ -126,6 +128,11 @@ def _check(st: int, what: str):
 def launch_count() -> int:
     """Kernels launched by libldpc.so since it was loaded."""
     return int(lib().ldpc_launch_count())
+
+
+def alloc_count() -> int:
+    """Device and pinned-host allocations libldpc.so has made since it was loaded."""
+    return int(lib().ldpc_alloc_count())
 
 
 class Graph:

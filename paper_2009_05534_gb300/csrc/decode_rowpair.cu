@@ -433,8 +433,9 @@ ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t sme
     }
     NoAllocScratch *d = g_noalloc_dev[dev];
     for (int k = 0; k < n_items; ++k) g_noalloc_host[k] = h_items[k];
-    // pageable source: the copy is staged before cudaMemcpyAsync returns, so the static
-    // staging array is free again for the next call
+    // pageable source: this relies on the behaviour CUDA documents for asynchronous copies
+    // from pageable host memory, which copy the source into a driver staging buffer before
+    // the call returns; the static staging array is then free for the next call
     if (cudaMemcpyAsync(d->items, g_noalloc_host, (size_t)n_items * sizeof(ListItem),
                         cudaMemcpyHostToDevice, stream) != cudaSuccess ||
         cudaMemsetAsync(&d->counter, 0, sizeof(int), stream) != cudaSuccess)

@@ -19,6 +19,16 @@ namespace ldpc {
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static std::atomic<uint64_t> g_allocs{0};
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(p, bytes);
+}
+cudaError_t pinned_alloc(void **p, size_t bytes) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocHost(p, bytes);
+}
+
 static std::mutex g_attr_mu;
 static std::map<std::pair<const void *, int>, size_t> g_dyn_smem;
 static std::map<std::tuple<const void *, int, int, size_t>, int> g_occupancy;
@@ -117,6 +127,8 @@ const char *ldpc_status_string(ldpc_status s) {
 
 uint64_t ldpc_launch_count(void) { return ldpc::g_launches.load(); }
 
+uint64_t ldpc_alloc_count(void) { return ldpc::g_allocs.load(); }
+
 ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, int Z,
                               ldpc_graph_t *out) {
     if (!out) return LDPC_ERR_INVALID_ARG;
@@ -165,10 +177,10 @@ ldpc_status ldpc_graph_create(const int16_t *base, int M_bg, int N_bg, int K_b, 
     cudaGetDevice(&g->device);
     ldpc_status st = LDPC_OK;
     const size_t q_bytes = sizeof(int) * 2 * Graph::kQueues;
-    if (cudaMalloc(&g->d_edges, sizeof(uint32_t) * E) != cudaSuccess ||
-        cudaMalloc(&g->d_row_ptr, sizeof(int) * (M_bg + 1)) != cudaSuccess ||
-        cudaMalloc(&g->d_status, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&g->d_queues, q_bytes) != cudaSuccess) {
+    if (ldpc::dev_alloc((void **)&g->d_edges, sizeof(uint32_t) * E) != cudaSuccess ||
+        ldpc::dev_alloc((void **)&g->d_row_ptr, sizeof(int) * (M_bg + 1)) != cudaSuccess ||
+        ldpc::dev_alloc((void **)&g->d_status, sizeof(int)) != cudaSuccess ||
+        ldpc::dev_alloc((void **)&g->d_queues, q_bytes) != cudaSuccess) {
         st = LDPC_ERR_OUT_OF_MEMORY;
     } else if (cudaMemcpy(g->d_edges, h_edges, sizeof(uint32_t) * E, cudaMemcpyHostToDevice) !=
                    cudaSuccess ||
@@ -375,8 +387,8 @@ ldpc_status ldpc_decode_rows_host_maps(ldpc_graph_t g, const void *llr_dev,
         ws.map_cap = 0;
         size_t cap = 256;
         while (cap < (size_t)batch) cap *= 2;
-        if (cudaMalloc(&ws.d_maps, 2 * cap * sizeof(int32_t)) != cudaSuccess ||
-            cudaMallocHost(&ws.h_maps, 2 * cap * sizeof(int32_t)) != cudaSuccess) {
+        if (ldpc::dev_alloc((void **)&ws.d_maps, 2 * cap * sizeof(int32_t)) != cudaSuccess ||
+            ldpc::pinned_alloc((void **)&ws.h_maps, 2 * cap * sizeof(int32_t)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(ws.d_maps);
             cudaFreeHost(ws.h_maps);
@@ -442,7 +454,7 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
         cudaFree(g->d_stage);
         g->d_stage = nullptr;
         g->stage_bytes = 0;
-        if (cudaMalloc(&g->d_stage, need) != cudaSuccess) {
+        if (ldpc::dev_alloc((void **)&g->d_stage, need) != cudaSuccess) {
             cudaGetLastError();
             return LDPC_ERR_OUT_OF_MEMORY;
         }
@@ -591,8 +603,8 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
         ws.cap = 0;
         size_t cap = 256;
         while (cap < (size_t)n_items) cap *= 2;
-        if (cudaMalloc(&ws.d_items, cap * sizeof(ldpc::ListItem)) != cudaSuccess ||
-            cudaMallocHost(&ws.h_items, cap * sizeof(ldpc::ListItem)) != cudaSuccess) {
+        if (ldpc::dev_alloc((void **)&ws.d_items, cap * sizeof(ldpc::ListItem)) != cudaSuccess ||
+            ldpc::pinned_alloc((void **)&ws.h_items, cap * sizeof(ldpc::ListItem)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(ws.d_items);
             cudaFreeHost(ws.h_items);
@@ -602,7 +614,7 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
         }
         ws.cap = cap;
     }
-    if (!ws.d_counter && cudaMalloc(&ws.d_counter, sizeof(int)) != cudaSuccess) {
+    if (!ws.d_counter && ldpc::dev_alloc((void **)&ws.d_counter, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return LDPC_ERR_OUT_OF_MEMORY;
     }

@@ -160,6 +160,11 @@ ldpc_status launch_list_noalloc(const ListItem *h_items, int n_items, size_t sme
 
 void count_launch();
 
+// Every device and pinned-host allocation the library makes goes through these two
+// (counted, exported through ldpc_alloc_count()).
+cudaError_t dev_alloc(void **p, size_t bytes);
+cudaError_t pinned_alloc(void **p, size_t bytes);
+
 // Launch set-up kept off the per-call path: a kernel's dynamic shared-memory limit is set
 // only when a launch asks for a different amount than the last one on this device, and
 // occupancy answers are remembered per (kernel, device, threads, dynamic shared memory).

@@ -35,8 +35,8 @@ extern "C" ldpc_status ldpc_selftest_wait_timeout(unsigned int spin_limit, ldpc_
     if (spin_limit == 0 || spin_limit > ldpc::tm::kSpinLimit) return LDPC_ERR_INVALID_ARG;
     int *d_status = nullptr;
     unsigned long long *d_cycles = nullptr;
-    if (cudaMalloc(&d_status, sizeof(int)) != cudaSuccess) return LDPC_ERR_OUT_OF_MEMORY;
-    if (cudaMalloc(&d_cycles, sizeof(unsigned long long)) != cudaSuccess) {
+    if (ldpc::dev_alloc((void **)&d_status, sizeof(int)) != cudaSuccess) return LDPC_ERR_OUT_OF_MEMORY;
+    if (ldpc::dev_alloc((void **)&d_cycles, sizeof(unsigned long long)) != cudaSuccess) {
         cudaFree(d_status);
         return LDPC_ERR_OUT_OF_MEMORY;
     }

@@ -82,3 +82,29 @@ def test_noalloc_rejects_oversize_list(ldpc):
         ldpc.decode_list_noalloc(big)
     for g in graphs.values():
         g.close()
+
+
+def test_noalloc_allocates_nothing(ldpc):
+    """The entry point's distinguishing claim: on a stream the library has never seen, the
+    regular work-list decode allocates its per-stream workspace, the allocation-free one
+    does not (the library counts every device and pinned-host allocation it makes)."""
+    graphs, keep, table = _items(ldpc, 8, 77)
+    n = len(table)
+    bits = torch.zeros((n, 1056), dtype=torch.uint8, device="cuda")
+    iters = torch.zeros((n,), dtype=torch.int32, device="cuda")
+    t = table.copy()
+    t["hard_bits"] = bits.data_ptr() + np.arange(n) * 1056
+    t["iters"] = iters.data_ptr() + np.arange(n) * 4
+    ldpc.decode_list_noalloc(t)                   # set-up on this device done before counting
+    torch.cuda.synchronize()
+    fresh = torch.cuda.Stream()
+    before = ldpc.alloc_count()
+    for _ in range(2):
+        ldpc.decode_list_noalloc(t, stream=fresh)
+    torch.cuda.synchronize()
+    assert ldpc.alloc_count() == before
+    ldpc.decode_list_array(t, stream=torch.cuda.Stream())   # a new stream's workspace
+    torch.cuda.synchronize()
+    assert ldpc.alloc_count() > before
+    for g in graphs.values():
+        g.close()
