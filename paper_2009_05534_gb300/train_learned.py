@@ -175,11 +175,18 @@ def main(argv=None):
                     help="with --loss every: each iteration's parameters follow their own "
                          "term (local) or the whole unrolled chain (full)")
     ap.add_argument("--checkpoint", default=None)
+    ap.add_argument("--eval-only", action="store_true",
+                    help="re-evaluate the table already in --out (no training): BLER sweep of "
+                         "--eval-codewords fresh codewords per point over --eval-grid, "
+                         "written into the file's eval record")
     ap.add_argument("--out", required=True)
     a = ap.parse_args(argv)
 
     def log(msg):
         print(f"[{time.strftime('%H:%M:%S')}] {msg}", flush=True)
+
+    if a.eval_only:
+        return evaluate_only(a, log)
 
     t0 = time.time()
     llr, cw, n_rows, base = training_set(a.kind, a.Z, a.codewords, a.batch, a.ebn0_lo,
@@ -223,6 +230,34 @@ def main(argv=None):
                  "bler_plain": curves["plain"], "bler_learned": curves["learned"],
                  "ebn0_at_bler_1e-2": res},
     }
+    save_table(a.out, table, meta)
+    log(f"wrote {a.out}")
+    graph.close()
+
+
+def evaluate_only(a, log):
+    """BLER sweep of a trained table against plain min-sum on fresh codewords; the table
+    file's eval record is replaced by the new one."""
+    import torch
+    from synth import SHAPES, make_workload
+    table, meta = load_table(a.out)
+    T = int(meta["T"])
+    wl0 = make_workload(a.kind, a.Z, 1, 1.0, seed=0, graph_seed=0)
+    graph = Graph(wl0.base, SHAPES[a.kind].K_b, a.Z)
+    lo, hi, st = (float(x) for x in a.eval_grid.split(":"))
+    grid = [round(lo + k * st, 4) for k in range(int(round((hi - lo) / st)) + 1)]
+    seed = int(meta.get("eval", {}).get("seed", a.seed + 1)) + 100_000
+    t0 = time.time()
+    curves = bler_sweep(graph, a.kind, a.Z, T, {"plain": None,
+                                                "learned": torch.from_numpy(table).cuda()},
+                        grid, a.eval_codewords, a.batch, seed, log=log)
+    res = {name: ebn0_at(grid, curves[name], 1e-2) for name in curves}
+    log(f"Eb/N0 at BLER 1e-2: {res}")
+    meta["eval"] = {"codewords_per_point": a.eval_codewords,
+                    "codewords_total": a.eval_codewords * len(grid), "seed": seed,
+                    "llr": "binary16", "early_stop": False, "ebn0_db": grid,
+                    "bler_plain": curves["plain"], "bler_learned": curves["learned"],
+                    "ebn0_at_bler_1e-2": res, "eval_s": round(time.time() - t0, 1)}
     save_table(a.out, table, meta)
     log(f"wrote {a.out}")
     graph.close()
