@@ -245,6 +245,13 @@ def test_fp16_hand_example(ldpc):
     graph.sync_status()
     assert post.cpu().double().numpy()[0].tolist() == lx["post"]
     assert c2v.cpu().double().numpy()[0].tolist() == lx["c2v"]
+    ox = g["offset_0.3_T1"]
+    _, _, post, c2v = ldpc.decode(graph, llr, 1, early_stop=False, punct_cols=0,
+                                  n_rows=code["n_rows"], debug=True, algo=ldpc.OFFSET,
+                                  offset=0.3)
+    torch.cuda.synchronize()
+    assert post.cpu().double().numpy()[0].tolist() == ox["post"]
+    assert c2v.cpu().double().numpy()[0].tolist() == ox["c2v"]
     graph.close()
 
 

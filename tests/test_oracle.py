@@ -102,6 +102,12 @@ def test_hand_example_binary16_z2():
                               want_c2v=True)
     assert r.post[0].astype(np.float64).tolist() == lx["post"]
     assert r.c2v[0].astype(np.float64).tolist() == lx["c2v"]
+    ox = g["offset_0.3_T1"]
+    r = oracle.decode_layered(base, code["K_b"], code["Z"], code["n_rows"], llr,
+                              algo=oracle.OFFSET, offset=0.3, max_iter=1, early_stop=False,
+                              punct=0, want_post=True, want_c2v=True)
+    assert r.post[0].astype(np.float64).tolist() == ox["post"]
+    assert r.c2v[0].astype(np.float64).tolist() == ox["c2v"]
 
 
 # ------------------------------------------------------------- P3: check-node closed form
