@@ -27,14 +27,15 @@
 // along without writing anything.
 //
 // Arithmetic (exact on these integers, so bit-identical to 8-bit fixed point): posteriors
-// as binary16 L + 1279 in shared memory (on [1152, 1406] binary16 has spacing 1; word
+// as binary16 L + 1152 in shared memory (on [1025, 1279] binary16 has spacing 1; word
 // (c, i) holds the two codewords' values), messages as bytes c + 128 in Tensor Memory
 // (edge e at column e/2, byte 2(e%2) + lane), turned into binary16 c + 1152 by one PRMT
-// under the exponent byte 0x64, so v + 127 = (L + 1279) - (c + 1152) is one subtraction;
-// saturation of v by two relu FMAs (y = max(v + 127, 0), z = max(254 - y, 0),
-// sat(v) = 127 - z); min.xorsign.abs for m1 and the sign product, plain min / max for m2;
-// new magnitude max(m1', (m1 + m2 - 1) - |v|), which is m2' on the argmin edge and m1'
-// elsewhere, so no argmin index is kept.
+// under the exponent byte 0x64, so v = (L + 1152) - (c + 1152) is one subtraction and
+// sat(v) one min and one max (1-cycle ALU operations); min.xorsign.abs for m1 and the sign
+// product, plain min / max for m2, both as a tree over the row's edges; new magnitude
+// max(m1', (m1 + m2 - 1) - |v|), which is m2' on the argmin edge and m1' elsewhere, so no
+// argmin index is kept; the new posterior (x + c') + 1152 is the new message c' + 1152
+// plus x, clamped to [1025, 1279].
 #include "f16x2.h"
 #include "ldpc_internal.h"
 #include "tmem.h"
@@ -91,24 +92,20 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
         // unless the circulant wraps row i
         off[j] = min(i4 + (uint32_t)mt.s4, i4z + (uint32_t)mt.s4) + (uint32_t)mt.col4;
     }
-    // the layer barrier: the previous layer's posterior stores are visible after it; the
-    // dispatch to this row's code, its messages and its addresses are ready before it
     named_sync(1, nthr);
 #pragma unroll
     for (int j = 0; j < D; ++j) X[j] = *reinterpret_cast<const uint32_t *>(Lbytes + off[j]);
     twait_ld();
-    uint32_t m1 = kInf2, m2 = kInf2;
+    uint32_t M[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+        M[j] = prmt(cm[(P + j) >> 1], 0x64646464u, ((P + j) & 1) ? 0x4342u : 0x4140u);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const uint32_t M =
-            prmt(cm[(P + j) >> 1], 0x64646464u, ((P + j) & 1) ? 0x4342u : 0x4140u);
-        const uint32_t y = h2relu_fma(M, kNegOne2, X[j]);   // max(v + 127, 0)
-        const uint32_t z = h2relu_fma(y, kNegOne2, k254);   // max(254 - y, 0)
-        const uint32_t x = h2sub(kP127, z);                 // sat(v)
-        m2 = h2min(m2, h2max(h2abs(m1), h2abs(x)));
-        m1 = h2minxs(m1, x);
-        X[j] = x;
+        X[j] = h2min(h2max(h2sub(X[j], M[j]), kNeg127), kP127);   // sat(v), v = L - c
     }
+    uint32_t m1, m2;
+    min_tree<0, D>(X, m1, m2);
     const uint32_t SO = (m1 & kSign2) | kOne2;
     const uint32_t a1 = m1 & kAbs2;
     const uint32_t m1c = h2relu_fma(a1, kOne2, kNegOne2);
@@ -120,8 +117,8 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
         const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
         const uint32_t sg = (x & kSign2) ^ SO;
         C[j] = h2fma(ex, sg, kBias2);                          // c' + 1152
-        uint32_t L = h2add(C[j], h2add(x, kP127));             // (x + c') + 1279
-        L = h2max(h2min(L, kPostHi), kPostLo);
+        uint32_t L = h2add(C[j], x);                           // (x + c') + 1152
+        L = h2max(h2min(L, kPost1152Hi), kPost1152Lo);
         if (store) *reinterpret_cast<uint32_t *>(Lbytes + off[j]) = L;
     }
 #pragma unroll
@@ -171,7 +168,7 @@ __device__ __forceinline__ uint32_t pq_parity(const EdgeMetaQ *meta, const unsig
         const EdgeMetaQ mt = meta[e0 + j];
         const uint32_t off =
             min(i4 + (uint32_t)mt.s4, i4z + (uint32_t)mt.s4) + (uint32_t)mt.col4;
-        par ^= h2lt_mask(*reinterpret_cast<const uint32_t *>(Lbytes + off), kPostBias);
+        par ^= h2lt_mask(*reinterpret_cast<const uint32_t *>(Lbytes + off), kBias2);
     }
     return par;
 }
@@ -300,11 +297,11 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
             pending &= ~(1u << S);
             src = stage + S * pp.stage_bytes;
         }
-        // binary16 L + 1279 = 1024 + (L + 255): bit pattern 0x6400 + L + 255
+        // binary16 L + 1152 = 1024 + (L + 128): bit pattern 0x6400 + L + 128
         for (int j = tid; j < NV; j += nthr) {
             const int t0 = j - lo;
             const int q = (t0 >= 0 && t0 < p.n_tx) ? (int)src[t0] : 0;
-            Lh[2 * j + X] = (uint16_t)(0x64FF + q);
+            Lh[2 * j + X] = (uint16_t)(0x6480 + q);
         }
         return true;
     };
@@ -320,7 +317,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
             unsigned x = 0;
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-                x |= (((wv[kk] >> sh) & 0xffffu) < 0x64FFu ? 1u : 0u) << kk;
+                x |= (((wv[kk] >> sh) & 0xffffu) < 0x6480u ? 1u : 0u) << kk;
             const int rest = K - 8 * b;
             if (rest < 8) x &= (1u << rest) - 1u;
             p.bits[out_row(p, cw[X]) * nbytes + b] = (uint8_t)x;
@@ -328,7 +325,7 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
         if (tid == 0) p.iters[out_row(p, cw[X])] = t[X];
         if (p.post) {
             int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw[X] * NV;
-            for (int j = tid; j < NV; j += nthr) po[j] = (int8_t)((int)Lh[2 * j + X] - 0x64FF);
+            for (int j = tid; j < NV; j += nthr) po[j] = (int8_t)((int)Lh[2 * j + X] - 0x6480);
         }
         if (p.c2v) {
             twait_st();

@@ -20,6 +20,10 @@ constexpr uint32_t kPostBias = 0x64FF64FFu;   // 1279: L = 0
 constexpr uint32_t kPostLo = 0x64806480u;     // 1152: L = -127
 constexpr uint32_t kPostHi = 0x657E657Eu;     // 1406: L = 127
 constexpr uint32_t k254 = 0x5BF05BF0u;        // 254.0
+// int8 posteriors biased by 1152 (the message bias): L + 1152 on [1025, 1279]
+constexpr uint32_t kNeg127 = 0xD7F0D7F0u;     // -127.0
+constexpr uint32_t kPost1152Lo = 0x64016401u; // 1025: L = -127
+constexpr uint32_t kPost1152Hi = 0x64FF64FFu; // 1279: L = 127
 
 
 
@@ -82,6 +86,34 @@ __device__ __forceinline__ uint32_t h2lt_mask(uint32_t a, uint32_t b) {
     return d;
 }
 
+// m1 (the smallest |x| of x[LO .. LO + N), carrying the product of their signs) and m2
+// (the second smallest |x|) as a tree: two values give m1 = min.xorsign(a, b) and
+// m2 = max(|a|, |b|); two halves combine as m1 = min.xorsign(m1a, m1b) and
+// m2 = min(m2a, m2b, max(|m1a|, |m1b|)); one value gives m1 = x, m2 = +inf.  Every step is
+// an exact min / max, so the result equals the edge-by-edge scan, with 3N - 4 operations
+// (N >= 2) instead of 3N and a dependent chain of about log2 N steps instead of N.
+template <int LO, int N, int D>
+__device__ __forceinline__ void min_tree(const uint32_t (&x)[D], uint32_t &m1, uint32_t &m2) {
+    if constexpr (N == 1) {
+        m1 = x[LO];
+        m2 = kInf2;
+    } else if constexpr (N == 2) {
+        m1 = h2minxs(x[LO], x[LO + 1]);
+        m2 = h2max(h2abs(x[LO]), h2abs(x[LO + 1]));
+    } else if constexpr (N == 3) {
+        uint32_t a1, a2;
+        min_tree<LO, 2>(x, a1, a2);
+        m1 = h2minxs(a1, x[LO + 2]);
+        m2 = h2min(a2, h2max(h2abs(a1), h2abs(x[LO + 2])));
+    } else {
+        constexpr int NA = 2 * ((N / 2 + 1) / 2);    // even, and N - NA >= 2
+        uint32_t a1, a2, b1, b2;
+        min_tree<LO, NA>(x, a1, a2);
+        min_tree<LO + NA, N - NA>(x, b1, b2);
+        m1 = h2minxs(a1, b1);
+        m2 = h2min(h2min(a2, b2), h2max(h2abs(a1), h2abs(b1)));
+    }
+}
 
 }  // namespace h2
 }  // namespace ldpc
