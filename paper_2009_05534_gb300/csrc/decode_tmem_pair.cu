@@ -77,12 +77,17 @@ struct PairParams {
 template <int D, int P>
 __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lbytes,
                                        uint32_t tcolumn, int e0, uint32_t i4, uint32_t i4z,
-                                       bool store, int nthr) {
+                                       bool store, int nthr, uint32_t &carry) {
     constexpr int NC = (P + D + 1) / 2;
     uint32_t cm[NC];
-    // a row that starts mid-column reads the column the previous row has just stored
-    if constexpr (P == 1) twait_st();
-    tload<NC>(tcolumn, cm);
+    // a row that starts mid-column takes that column from the previous row's registers
+    // (its upper half, this row's first message, passed through the previous row intact)
+    if constexpr (P == 1) {
+        cm[0] = carry;
+        tload<NC - 1>(tcolumn + 1, cm + 1);
+    } else {
+        tload<NC>(tcolumn, cm);
+    }
     uint32_t X[D];
     uint32_t off[D];
 #pragma unroll
@@ -132,22 +137,25 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
         else
             cm[k] = prmt(cm[k], C[ih], 0x6410u);
     }
+    // the previous row's store to the shared column lands before this one
+    if constexpr (P == 1) twait_st();
     tstore<NC>(tcolumn, cm);
+    if constexpr (((P + D) & 1) == 1) carry = cm[NC - 1];
 }
 
 // One dispatch per row on key = 2 D + P (the row's degree and the parity of its first
 // edge), computed a row ahead; the branch happens before the row's layer barrier.
 __device__ __forceinline__ void pq_dispatch(int key, const EdgeMetaQ *meta, unsigned char *Lbytes,
                                             uint32_t tbase, int e0, uint32_t i4, uint32_t i4z,
-                                            bool store, int nthr) {
+                                            bool store, int nthr, uint32_t &carry) {
     const uint32_t tc = tbase + (uint32_t)(e0 >> 1);
     switch (key) {
 #define LDPC_PQ_CASE(D)                                                   \
     case 2 * D:                                                           \
-        pq_row<D, 0>(meta, Lbytes, tc, e0, i4, i4z, store, nthr);         \
+        pq_row<D, 0>(meta, Lbytes, tc, e0, i4, i4z, store, nthr, carry);  \
         break;                                                            \
     case 2 * D + 1:                                                       \
-        pq_row<D, 1>(meta, Lbytes, tc, e0, i4, i4z, store, nthr);         \
+        pq_row<D, 1>(meta, Lbytes, tc, e0, i4, i4z, store, nthr, carry);  \
         break;
         LDPC_PQ_CASE(2) LDPC_PQ_CASE(3) LDPC_PQ_CASE(4) LDPC_PQ_CASE(5) LDPC_PQ_CASE(6)
         LDPC_PQ_CASE(7) LDPC_PQ_CASE(8) LDPC_PQ_CASE(9) LDPC_PQ_CASE(10) LDPC_PQ_CASE(11)
@@ -155,7 +163,7 @@ __device__ __forceinline__ void pq_dispatch(int key, const EdgeMetaQ *meta, unsi
         LDPC_PQ_CASE(17) LDPC_PQ_CASE(18) LDPC_PQ_CASE(19) LDPC_PQ_CASE(20)
 #undef LDPC_PQ_CASE
     default:
-        break;
+        __builtin_unreachable();
     }
 }
 
@@ -356,13 +364,14 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
 #pragma unroll 1
     while (!failed && (cw[0] >= 0 || cw[1] >= 0)) {
         int e0 = s_row[0], key = s_key[0];
+        uint32_t carry = 0u;                         // set by a row that ends mid-column
         twait_st();                                  // rows starting on a column do not wait
 #pragma unroll 1
         for (int r = 0; r < n_rows; ++r) {
             const int e0r = e0, keyr = key;
             e0 = s_row[r + 1];                       // the next row's, read before the barrier
             key = s_key[r + 1];
-            pq_dispatch(keyr, s_meta, Lbytes, tbase, e0r, i4, i4z, store, nthr);
+            pq_dispatch(keyr, s_meta, Lbytes, tbase, e0r, i4, i4z, store, nthr, carry);
         }
         named_sync(1, nthr);                         // the iteration's last layer is done
         ++t[0];
