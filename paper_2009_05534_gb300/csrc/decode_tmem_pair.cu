@@ -137,10 +137,14 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
         else
             cm[k] = prmt(cm[k], C[ih], 0x6410u);
     }
-    // the previous row's store to the shared column lands before this one
-    if constexpr (P == 1) twait_st();
-    tstore<NC>(tcolumn, cm);
-    if constexpr (((P + D) & 1) == 1) carry = cm[NC - 1];
+    // a column shared with the next row is stored by that row (its lower half travels in
+    // carry), so every column is stored once per iteration
+    if constexpr (((P + D) & 1) == 1) {
+        tstore<NC - 1>(tcolumn, cm);
+        carry = cm[NC - 1];
+    } else {
+        tstore<NC>(tcolumn, cm);
+    }
 }
 
 // One dispatch per row on key = 2 D + P (the row's degree and the parity of its first
@@ -373,6 +377,8 @@ __global__ void __launch_bounds__(kThreadsQ, 1) pair_kernel(const __grid_constan
             key = s_key[r + 1];
             pq_dispatch(keyr, s_meta, Lbytes, tbase, e0r, i4, i4z, store, nthr, carry);
         }
+        // the last row ends mid-column when E is odd: its last column has no next row
+        if (E & 1) tstore<1>(tbase + (uint32_t)(E >> 1), &carry);
         named_sync(1, nthr);                         // the iteration's last layer is done
         ++t[0];
         ++t[1];
