@@ -345,6 +345,31 @@ uint64_t ldpc_launch_count(void);
  * diagnostic. */
 uint64_t ldpc_alloc_count(void);
 
+/* The 8-bit batch kernel (threads_per_row 1; the layered schedule of Sec. III) compiled at
+ * run time for the degree sequence of the rows a decode uses, so that the layers of an
+ * iteration run as straight-line code instead of one indirect branch per row.  Compiling
+ * (NVRTC) takes a few seconds of host time per new degree sequence; the module is then
+ * kept for the process's lifetime.  Results are bit-identical to the generic kernel's,
+ * which runs whenever no compiled kernel is ready.
+ *   mode 0: off.
+ *   mode 1 (the default): a new sequence is compiled on a background thread; decodes use
+ *           the generic kernel until it is ready.
+ *   mode 2: the decode that meets a new sequence compiles it and waits (for throughput
+ *           runs: compile during warm-up).
+ *   any other value: no change.
+ * Returns the mode before the call (bits 0-1), plus 4 once a kernel has been compiled and
+ * loaded and 8 once a compilation or load has failed since the library was loaded.
+ * Process-wide; never fails. */
+int ldpc_pair_jit(int mode);
+
+/* Compile (and wait for) the batch kernel of ldpc_pair_jit for a degree sequence:
+ * row_degrees (host, n_rows entries, each 2..20) are the degrees of the rows a decode will
+ * use, in order.  Host work only (no CUDA call; the first decode with the sequence loads
+ * the module), so a throughput run can compile before its warm-up.  Returns LDPC_OK
+ * (compiled now or earlier), LDPC_ERR_INVALID_ARG for a bad sequence, LDPC_ERR_UNSUPPORTED
+ * when the compilation failed (decodes then use the generic kernel). */
+ldpc_status ldpc_pair_jit_prepare(const int *row_degrees, int n_rows);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,7 +55,8 @@ ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_dest
                "ldpc_learned_workspace_floats", "ldpc_learned_forward", "ldpc_learned_backward",
                "ldpc_learned_forward_iter", "ldpc_learned_backward_iter",
                "ldpc_flooding_workspace_floats", "ldpc_decode_flooding", "ldpc_decode_rows",
-               "ldpc_decode_rows_host_maps", "ldpc_selftest_wait_timeout", "ldpc_alloc_count")
+               "ldpc_decode_rows_host_maps", "ldpc_selftest_wait_timeout", "ldpc_alloc_count",
+               "ldpc_pair_jit", "ldpc_pair_jit_prepare")
 
 
 def lib():
@@ -103,6 +104,10 @@ def lib():
             L.ldpc_launch_count.restype = ctypes.c_uint64
             L.ldpc_alloc_count.argtypes = []
             L.ldpc_alloc_count.restype = ctypes.c_uint64
+            L.ldpc_pair_jit.argtypes = [i]
+            L.ldpc_pair_jit.restype = i
+            L.ldpc_pair_jit_prepare.argtypes = [P, i]
+            L.ldpc_pair_jit_prepare.restype = i
             L.ldpc_decode_rows.argtypes = [P, P, P, P, i, i, P, ctypes.POINTER(DecodeOpts),
                                            P, P]
             L.ldpc_decode_rows.restype = i
@@ -133,6 +138,26 @@ def launch_count() -> int:
 def alloc_count() -> int:
     """Device and pinned-host allocations libldpc.so has made since it was loaded."""
     return int(lib().ldpc_alloc_count())
+
+
+def pair_jit(mode: int = -1) -> int:
+    """The per-graph compiled batch kernel: 0 off, 1 compile in the background (default),
+    2 compile at first use and wait, -1 only query.  Returns the previous mode (bits 0-1),
+    plus 4 once a kernel has been compiled and 8 once a compilation has failed
+    (ldpc_pair_jit)."""
+    return int(lib().ldpc_pair_jit(int(mode)))
+
+
+def pair_jit_prepare(base, n_rows: int = 0) -> None:
+    """Compile the per-graph batch kernel for the first n_rows rows (0: all) of a base
+    table (int array [M][N], -1 = no circulant) and wait (ldpc_pair_jit_prepare); raises
+    when the sequence is invalid or the compilation failed."""
+    import numpy as np
+    b = np.asarray(base)
+    n = int(n_rows) or b.shape[0]
+    deg = np.ascontiguousarray((b[:n] >= 0).sum(axis=1), dtype=np.int32)
+    _check(lib().ldpc_pair_jit_prepare(deg.ctypes.data_as(ctypes.c_void_p), n),
+           "ldpc_pair_jit_prepare")
 
 
 class Graph:

@@ -24,7 +24,36 @@ def _nvcc() -> str:
 
 def _flags():
     return ["-O3", "-std=c++17", GENCODE, "-lineinfo", "-Xcompiler", "-fPIC",
-            "-Xptxas", "-O3", "--expt-relaxed-constexpr"]
+            "-Xptxas", "-O3", "--expt-relaxed-constexpr", "-I", BUILD]
+
+
+# Headers the runtime compiler needs for the per-graph batch kernels (pair_jit.cu), under
+# the names by which pair_kernel.cuh includes them.
+JIT_FILES = (("pair_kernel.cuh", os.path.join(CSRC, "pair_kernel.cuh")),
+             ("f16x2.h", os.path.join(CSRC, "f16x2.h")),
+             ("ldpc_params.h", os.path.join(CSRC, "ldpc_params.h")),
+             ("tmem.h", os.path.join(CSRC, "tmem.h")))
+JIT_HEADER = os.path.join(BUILD, "ldpc_jit_sources.h")
+
+
+def _write_jit_sources() -> None:
+    """Embed the kernel headers as string literals (rewritten only when they change)."""
+    out = ["// Generated by build.py: the headers of pair_kernel.cuh for the runtime compiler.",
+           "#pragma once", "namespace ldpc {", "namespace jitsrc {",
+           "struct File { const char *name; const char *text; };",
+           "static const File kFiles[] = {"]
+    for name, path in JIT_FILES:
+        text = open(path).read()
+        if ")LDPCSRC" in text:
+            raise RuntimeError(f"{path}: contains the raw-string delimiter")
+        out.append(f'    {{"{name}", R"LDPCSRC({text})LDPCSRC"}},')
+    out += ["};", "}  // namespace jitsrc", "}  // namespace ldpc", ""]
+    body = "\n".join(out)
+    if not os.path.exists(JIT_HEADER) or open(JIT_HEADER).read() != body:
+        tmp = JIT_HEADER + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            f.write(body)
+        os.replace(tmp, JIT_HEADER)
 
 
 def _stale(obj: str, src: str, headers: list[str]) -> bool:
@@ -37,9 +66,11 @@ def _stale(obj: str, src: str, headers: list[str]) -> bool:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
+    _write_jit_sources()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.h")) +
-                     glob.glob(os.path.join(HERE, "..", "include", "*.h")))
+                     glob.glob(os.path.join(CSRC, "*.cuh")) +
+                     glob.glob(os.path.join(HERE, "..", "include", "*.h")) + [JIT_HEADER])
     objs = []
     jobs = []
     for s in srcs:
@@ -57,7 +88,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 raise RuntimeError(f"nvcc failed: {' '.join(j)}\n{r.stdout}\n{r.stderr}")
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [nvcc, GENCODE, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [nvcc, GENCODE, "-shared", "-o", tmp, *objs, "-lcudart", "-lnvrtc"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -1,7 +1,9 @@
 // binary16x2 helpers shared by the row-pair kernels (values held as 32-bit bit patterns).
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace ldpc {
 namespace h2 {

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/ldpc.h"
+#include "ldpc_params.h"
 
 namespace ldpc {
 
@@ -50,40 +51,6 @@ struct Graph {
 // (the kernel then falls back to a fixed assignment of codewords to blocks).
 int *graph_queue(Graph *g, cudaStream_t stream);
 
-// Everything a decode kernel needs, passed by value.
-struct DecodeParams {
-    const uint32_t *edges;    // device [E]
-    const int *row_ptr;       // device [n_rows + 1]
-    const uint32_t *h_edges;  // host copies of the same tables
-    const int *h_row_ptr;
-    int n_rows, E, Z, n_cols, K_b;
-    int max_deg;              // largest row degree among the used rows
-    int punct, n_tx, max_iter, early_stop, batch;
-    int algo;
-    float alpha, offset;
-    int offset_q;
-    const float *learned;     // [max_iter][n_rows][2] or null
-    const void *llr;          // [batch][n_tx]
-    uint8_t *bits;            // [batch][ceil(K/8)]
-    int32_t *iters;           // [batch]
-    void *post;               // [batch][n_cols * Z] or null
-    void *c2v;                // [batch][E * Z] or null
-    int *status;              // device status word
-    const int32_t *in_rows;   // [batch] LLR row of codeword b, or null (row b)
-    const int32_t *out_rows;  // [batch] output row of codeword b, or null (row b)
-    int threads_per_row;      // cooperating threads per row pair (0 = automatic)
-    int cluster_size;         // 1, or 2: one codeword per cluster of two blocks
-    int *queue;               // device [2] work counters of the launch's stream, or null
-};
-
-// source and destination rows of codeword b of a batch (identity without row maps)
-__host__ __device__ __forceinline__ size_t in_row(const DecodeParams &p, int b) {
-    return (size_t)(p.in_rows ? p.in_rows[b] : b);
-}
-__host__ __device__ __forceinline__ size_t out_row(const DecodeParams &p, int b) {
-    return (size_t)(p.out_rows ? p.out_rows[b] : b);
-}
-
 // One codeword of a work list (device side; built by ldpc_decode_list).
 struct ListItem {
     const uint32_t *edges;    // graph edge table
@@ -103,6 +70,9 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
 // Tensor Memory, per-lane stopping and refill (decode_tmem_pair.cu).
 bool pair_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_pair(const DecodeParams &p, cudaStream_t stream);
+// The batch kernel compiled at run time for the row sequence of p (pair_jit.cu), as a
+// launchable kernel handle, or null (compilation off or failed: the generic kernel runs).
+const void *pair_jit_kernel(const DecodeParams &p);
 
 // One codeword per cluster of two blocks on two SMs, each block half of the row pairs,
 // posterior updates exchanged through distributed shared memory (decode_cluster.cu).

@@ -5,7 +5,9 @@
 // 32-bit column per register, at warp-uniform run-time column addresses.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace ldpc {
 namespace tm {
