@@ -202,13 +202,16 @@ def measured_peaks():
 
 def profiled_traffic(kernel_tag: str):
     """DRAM bytes per launch recorded from ncu in profiles/, if the kernel source still
-    matches the hash recorded beside it (else None)."""
+    matches the hash recorded beside it (else None): sha256 of the kernel header and the
+    runtime-compilation unit that builds it for the graph, concatenated."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_2009_05534_gb300", "csrc", "decode_tmem_pair.cu")
+    csrc = os.path.join(ROOT, "paper_2009_05534_gb300", "csrc")
     try:
         text = open(path).read()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        blob = b"".join(open(os.path.join(csrc, f), "rb").read()
+                        for f in ("pair_kernel.cuh", "pair_jit.cu"))
+        h = hashlib.sha256(blob).hexdigest()[:16]
     except OSError:
         return None
     got, sha = None, None
