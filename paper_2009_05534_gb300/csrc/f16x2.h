@@ -22,10 +22,6 @@ constexpr uint32_t kPostBias = 0x64FF64FFu;   // 1279: L = 0
 constexpr uint32_t kPostLo = 0x64806480u;     // 1152: L = -127
 constexpr uint32_t kPostHi = 0x657E657Eu;     // 1406: L = 127
 constexpr uint32_t k254 = 0x5BF05BF0u;        // 254.0
-// int8 posteriors biased by 1152 (the message bias): L + 1152 on [1025, 1279]
-constexpr uint32_t kNeg127 = 0xD7F0D7F0u;     // -127.0
-constexpr uint32_t kPost1152Lo = 0x64016401u; // 1025: L = -127
-constexpr uint32_t kPost1152Hi = 0x64FF64FFu; // 1279: L = 127
 
 
 

@@ -27,15 +27,15 @@
 // along without writing anything.
 //
 // Arithmetic (exact on these integers, so bit-identical to 8-bit fixed point): posteriors
-// as binary16 L + 1152 in shared memory (on [1025, 1279] binary16 has spacing 1; word
+// as binary16 L + 1279 in shared memory (on [1152, 1406] binary16 has spacing 1; word
 // (c, i) holds the two codewords' values), messages as bytes c + 128 in Tensor Memory
 // (edge e at column e/2, byte 2(e%2) + lane), turned into binary16 c + 1152 by one PRMT
-// under the exponent byte 0x64, so v = (L + 1152) - (c + 1152) is one subtraction and
-// sat(v) one min and one max (1-cycle ALU operations); min.xorsign.abs for m1 and the sign
-// product, plain min / max for m2, both as a tree over the row's edges; new magnitude
-// max(m1', (m1 + m2 - 1) - |v|), which is m2' on the argmin edge and m1' elsewhere, so no
-// argmin index is kept; the new posterior (x + c') + 1152 is the new message c' + 1152
-// plus x, clamped to [1025, 1279].
+// under the exponent byte 0x64, so v + 127 = (L + 1279) - (c + 1152) is one subtraction;
+// x + 127 = sat(v) + 127 by a relu FMA and a min, sat(v) by one subtraction;
+// min.xorsign.abs for m1 and the sign product, plain min / max for m2, both as a tree over
+// the row's edges; new magnitude max(m1', (m1 + m2 - 1) - |v|), which is m2' on the argmin
+// edge and m1' elsewhere, so no argmin index is kept; the new posterior
+// (x + c') + 1279 = (c' + 1152) + (x + 127), clamped to [1152, 1406].
 #pragma once
 
 #include "f16x2.h"
@@ -59,6 +59,7 @@ constexpr int kMaxEdgesQ = 1024;
 constexpr int kMaxRowsQ = 64;
 constexpr int kTmemColsQ = 512;
 constexpr int kThreadsQ = 384;
+constexpr uint32_t kPostZero = 0x64FFu;   // binary16 1279: posterior L = 0
 
 struct PairParams {
     DecodeParams p;
@@ -90,7 +91,7 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
     } else {
         tload<NC>(tcolumn, cm);
     }
-    uint32_t X[D];
+    uint32_t X[D], XB[D];
     uint32_t off[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -109,7 +110,10 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
         M[j] = prmt(cm[(P + j) >> 1], 0x64646464u, ((P + j) & 1) ? 0x4342u : 0x4140u);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        X[j] = h2min(h2max(h2sub(X[j], M[j]), kNeg127), kP127);   // sat(v), v = L - c
+        // (L + 1279) - (c + 1152) = v + 127: its lower clamp in the relu FMA, the upper one
+        // by a min (x + 127 = min(max(v + 127, 0), 254)), then x = sat(v)
+        XB[j] = h2min(h2relu_fma(M[j], kNegOne2, X[j]), k254);
+        X[j] = h2sub(XB[j], kP127);
     }
     uint32_t m1, m2;
     min_tree<0, D>(X, m1, m2);
@@ -124,8 +128,8 @@ __device__ __forceinline__ void pq_row(const EdgeMetaQ *meta, unsigned char *Lby
         const uint32_t ex = h2max(m1c, h2sub(T1, h2abs(x)));
         const uint32_t sg = (x & kSign2) ^ SO;
         C[j] = h2fma(ex, sg, kBias2);                          // c' + 1152
-        uint32_t L = h2add(C[j], x);                           // (x + c') + 1152
-        L = h2max(h2min(L, kPost1152Hi), kPost1152Lo);
+        uint32_t L = h2add(C[j], XB[j]);                       // (x + c') + 1279
+        L = h2max(h2min(L, kPostHi), kPostLo);
         if (store) *reinterpret_cast<uint32_t *>(Lbytes + off[j]) = L;
     }
 #pragma unroll
@@ -184,7 +188,7 @@ __device__ __forceinline__ uint32_t pq_parity(const EdgeMetaQ *meta, const unsig
         const EdgeMetaQ mt = meta[e0 + j];
         const uint32_t off =
             min(i4 + (uint32_t)mt.s4, i4z + (uint32_t)mt.s4) + (uint32_t)mt.col4;
-        par ^= h2lt_mask(*reinterpret_cast<const uint32_t *>(Lbytes + off), kBias2);
+        par ^= h2lt_mask(*reinterpret_cast<const uint32_t *>(Lbytes + off), kPostBias);
     }
     return par;
 }
@@ -319,11 +323,11 @@ __device__ __forceinline__ void pair_body(const PairParams &pp) {
             pending &= ~(1u << S);
             src = stage + S * pp.stage_bytes;
         }
-        // binary16 L + 1152 = 1024 + (L + 128): bit pattern 0x6400 + L + 128
+        // binary16 L + 1279 = 1024 + (L + 255): bit pattern 0x6400 + L + 255
         for (int j = tid; j < NV; j += nthr) {
             const int t0 = j - lo;
             const int q = (t0 >= 0 && t0 < p.n_tx) ? (int)src[t0] : 0;
-            Lh[2 * j + X] = (uint16_t)(0x6480 + q);
+            Lh[2 * j + X] = (uint16_t)(kPostZero + q);
         }
         return true;
     };
@@ -339,7 +343,7 @@ __device__ __forceinline__ void pair_body(const PairParams &pp) {
             unsigned x = 0;
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-                x |= (((wv[kk] >> sh) & 0xffffu) < 0x6480u ? 1u : 0u) << kk;
+                x |= (((wv[kk] >> sh) & 0xffffu) < kPostZero ? 1u : 0u) << kk;
             const int rest = K - 8 * b;
             if (rest < 8) x &= (1u << rest) - 1u;
             p.bits[out_row(p, cw[X]) * nbytes + b] = (uint8_t)x;
@@ -347,7 +351,8 @@ __device__ __forceinline__ void pair_body(const PairParams &pp) {
         if (tid == 0) p.iters[out_row(p, cw[X])] = t[X];
         if (p.post) {
             int8_t *po = reinterpret_cast<int8_t *>(p.post) + (size_t)cw[X] * NV;
-            for (int j = tid; j < NV; j += nthr) po[j] = (int8_t)((int)Lh[2 * j + X] - 0x6480);
+            for (int j = tid; j < NV; j += nthr)
+                po[j] = (int8_t)((int)Lh[2 * j + X] - (int)kPostZero);
         }
         if (p.c2v) {
             twait_st();
