@@ -80,8 +80,9 @@ typedef enum {
  *                per thread block); 2 or 4 = the low-latency strategy (alpha threads split
  *                each row's circulants and combine min, sub-min and sign by a log2(alpha)
  *                step warp-shuffle reduce; one codeword per thread block); int8 only.
- *                0 = automatic: 2 when the batch is no larger than the SM count and the
- *                graph fits, else 1.  Results are identical for every value. */
+ *                0 = automatic: 1 when the batch kernel compiled for the graph's row
+ *                sequence is ready (ldpc_pair_jit) or the batch exceeds the SM count,
+ *                else 2 when the graph fits.  Results are identical for every value. */
 typedef struct {
     int llr_type;
     int algo;
