@@ -246,7 +246,7 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
     from paper_2009_05534_gb300.serve import GpuBackend, SlotScheduler, latency_stats, run_paced
     from synth import make_workload
     rng = np.random.default_rng(seed)
-    graphs, rows, ks, llrs = {}, [], [], []
+    graphs, rows, ks, llrs, row_tables = {}, [], [], [], {}
     for kind in ("BG1", "BG2"):
         for Zs in SERVE_ZS:
             for rate in SERVE_RATES:
@@ -255,6 +255,7 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
                                        seed=seed * 1000 + len(rows), graph_seed=0)
                     if (kind, Zs) not in graphs:
                         graphs[(kind, Zs)] = ldpc.Graph(wl.base, wl.K_b, Zs)
+                    row_tables[(kind, rate)] = (wl.base, wl.n_rows)
                     q = torch.from_numpy(wl.llr_int8()).cuda()
                     for b in range(2):
                         llrs.append(q[b])
@@ -286,7 +287,7 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
                                int(meta["T"]), 0)
         ldpc.decode(g_l, lpool[:8], learned.max_iter, algo=ldpc.LEARNED, learned=learned.table)
     be = GpuBackend(table, kreq, n_buffers=4096, kmax=kmax, n_streams=4, early_stop=True,
-                    learned=learned)
+                    learned=learned, row_tables=list(row_tables.values()))
     sch = SlotScheduler(be, slot_us=500.0, max_requests=total + 1)
     # warm-up: a few slots outside the measurement
     warm = SlotScheduler(GpuBackend(np.tile(pool, 4), np.tile(ks, 4), n_buffers=1024,
@@ -302,6 +303,7 @@ def serving_measure(n_slots: int, mean_tbs: float = 128.0, seed: int = 1, max_it
             float(counts.mean()), "p50_us": st.get("p50_us"), "p99_us": st.get("p99_us"),
             "max_us": st.get("max_us"), "gbps": float(kreq.sum()) / wall / 1e9,
             "max_iter": max_iter, "early_stop": True, "learned_tbs": n_learned,
+            "list_kernel": "compiled for the served row sequences (ldpc_list_jit_prepare)",
             "traffic": "BG1|BG2 x Z{32..384} x R{1/3..8/9} x QPSK/16QAM/64QAM int8"
                        + (f"; {learned_share:.3f} of blocks learned (BG2 Z=128 R=1/5 "
                           "binary16, 10 iterations)" if learned is not None else "")}

@@ -371,6 +371,18 @@ int ldpc_pair_jit(int mode);
  * when the compilation failed (decodes then use the generic kernel). */
 ldpc_status ldpc_pair_jit_prepare(const int *row_degrees, int n_rows);
 
+/* Compile the low-latency work-list kernel of ldpc_decode_list for a set of row sequences
+ * (a server's graphs and rates): sequence q has n_rows[q] rows whose degrees (2..20) follow
+ * those of sequence q - 1 in row_degrees (host arrays).  An item whose graph's first n_rows
+ * rows have one of these degree sequences then runs its layers as straight-line code
+ * instead of one indirect branch per row; other items run the generic row loop in the same
+ * launch.  Results are identical either way.  Host work only (NVRTC, seconds); the next
+ * ldpc_decode_list call loads the module and later calls use it.  n_seqs = 0 stops using
+ * compiled list kernels.  Returns LDPC_OK, LDPC_ERR_INVALID_ARG (bad sequences, more than
+ * 64 of them), LDPC_ERR_UNSUPPORTED (the compilation failed: lists keep the kernel they
+ * had).  ldpc_decode_list_noalloc always uses the generic kernel. */
+ldpc_status ldpc_list_jit_prepare(const int *row_degrees, const int *n_rows, int n_seqs);
+
 #ifdef __cplusplus
 }
 #endif

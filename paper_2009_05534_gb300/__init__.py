@@ -56,7 +56,7 @@ ABI_SYMBOLS = ("ldpc_decode_opts_default", "ldpc_graph_create", "ldpc_graph_dest
                "ldpc_learned_forward_iter", "ldpc_learned_backward_iter",
                "ldpc_flooding_workspace_floats", "ldpc_decode_flooding", "ldpc_decode_rows",
                "ldpc_decode_rows_host_maps", "ldpc_selftest_wait_timeout", "ldpc_alloc_count",
-               "ldpc_pair_jit", "ldpc_pair_jit_prepare")
+               "ldpc_pair_jit", "ldpc_pair_jit_prepare", "ldpc_list_jit_prepare")
 
 
 def lib():
@@ -108,6 +108,8 @@ def lib():
             L.ldpc_pair_jit.restype = i
             L.ldpc_pair_jit_prepare.argtypes = [P, i]
             L.ldpc_pair_jit_prepare.restype = i
+            L.ldpc_list_jit_prepare.argtypes = [P, P, i]
+            L.ldpc_list_jit_prepare.restype = i
             L.ldpc_decode_rows.argtypes = [P, P, P, P, i, i, P, ctypes.POINTER(DecodeOpts),
                                            P, P]
             L.ldpc_decode_rows.restype = i
@@ -158,6 +160,24 @@ def pair_jit_prepare(base, n_rows: int = 0) -> None:
     deg = np.ascontiguousarray((b[:n] >= 0).sum(axis=1), dtype=np.int32)
     _check(lib().ldpc_pair_jit_prepare(deg.ctypes.data_as(ctypes.c_void_p), n),
            "ldpc_pair_jit_prepare")
+
+
+def list_jit_prepare(tables) -> None:
+    """Compile the work-list kernel for the row sequences of (base table, n_rows) pairs
+    (n_rows 0: every row) and wait (ldpc_list_jit_prepare); an empty list stops using
+    compiled list kernels.  Raises when a sequence is invalid or the compilation failed."""
+    import numpy as np
+    degs, rows = [], []
+    for base, n_rows in tables:
+        b = np.asarray(base)
+        n = int(n_rows) or b.shape[0]
+        degs.append((b[:n] >= 0).sum(axis=1))
+        rows.append(n)
+    d = np.ascontiguousarray(np.concatenate(degs) if degs else np.zeros(1), dtype=np.int32)
+    r = np.ascontiguousarray(rows if rows else [0], dtype=np.int32)
+    _check(lib().ldpc_list_jit_prepare(d.ctypes.data_as(ctypes.c_void_p),
+                                       r.ctypes.data_as(ctypes.c_void_p), len(rows)),
+           "ldpc_list_jit_prepare")
 
 
 class Graph:

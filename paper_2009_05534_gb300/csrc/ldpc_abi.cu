@@ -550,6 +550,8 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
     v.reserve((size_t)n_items);
     size_t smem = 0, smem_ll = 0;
     bool ll_ok = o.threads_per_row != 1;
+    // the compiled list kernel of the graphs' row sequences, if one has been prepared
+    const ldpc::ListModule *lm = ll_ok ? ldpc::list_jit_active() : nullptr;
     for (int k = 0; k < n_items; ++k) {
         const ldpc_work_item &w = items[k];
         if (!w.graph || !w.llr || !w.hard_bits || !w.iters) return LDPC_ERR_INVALID_ARG;
@@ -580,6 +582,7 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
         it.n_tx = n_tx;
         it.punct = 2;
         it.max_iter = w.max_iter;
+        it.seq = ldpc::list_jit_seq(lm, g, n_rows);
         smem = std::max(smem, ldpc::list_item_smem_bytes(E, n_rows, n_cols, g->Z));
         ll_ok = ll_ok && ldpc::list_ll_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows],
                                                       g->slots2_upto[n_rows]);
@@ -630,7 +633,7 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
         return LDPC_ERR_CUDA;
     if (ll_ok)
         return ldpc::launch_list_ll(ws.d_items, n_items, ws.d_counter, smem_ll,
-                                    o.early_stop ? 1 : 0, s);
+                                    o.early_stop ? 1 : 0, s, ldpc::list_jit_kernel(lm));
     return ldpc::launch_list(ws.d_items, n_items, ws.d_counter, smem, o.early_stop ? 1 : 0, s);
 }
 
@@ -687,6 +690,7 @@ static ldpc_status prepare_list_noalloc(const ldpc_work_item *items, int n_items
         it.n_tx = n_tx;
         it.punct = 2;
         it.max_iter = w.max_iter;
+        it.seq = -1;                             // the generic list kernels only
         smem = std::max(smem, ldpc::list_item_smem_bytes(E, n_rows, n_cols, g->Z));
         ll_ok = ll_ok && ldpc::list_ll_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows],
                                                       g->slots2_upto[n_rows]);

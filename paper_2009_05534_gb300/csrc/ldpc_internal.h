@@ -1,6 +1,7 @@
 // Internal definitions shared by the C-ABI entry points and the decoder kernels.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 #include <cuda_runtime.h>
@@ -45,22 +46,14 @@ struct Graph {
     int *d_queues = nullptr;              // device [kQueues][2]
     cudaStream_t q_stream[kQueues] = {};
     int n_queues = 0;
+    // per row count: (generation of a compiled list module << 32) | (1 + the case of this
+    // graph's row sequence in it, 0 = none); list_jit.cu
+    std::atomic<uint64_t> list_seq[kMaxRows + 1] = {};
 };
 
 // The work-counter pair of `g` for decodes on `stream`, or null when every slot is taken
 // (the kernel then falls back to a fixed assignment of codewords to blocks).
 int *graph_queue(Graph *g, cudaStream_t stream);
-
-// One codeword of a work list (device side; built by ldpc_decode_list).
-struct ListItem {
-    const uint32_t *edges;    // graph edge table
-    const int *row_ptr;       // graph row pointers
-    const int8_t *llr;        // [n_tx]
-    uint8_t *bits;            // [ceil(K/8)]
-    int32_t *iters;           // [1]
-    int Z, K_b, n_rows, n_cols;
-    int E, n_tx, punct, max_iter;
-};
 
 // Launch entry for the layered decoder (decode_layered.cu).  Returns LDPC_OK or an error
 // found while configuring the launch.
@@ -116,8 +109,16 @@ size_t list_item_smem_bytes(int E, int n_rows, int n_cols, int Z);
 // row pair, messages in Tensor Memory; slots2 = sum of ceil(degree / 2) over the item's rows.
 bool list_ll_item_supported(int Z, int E, int n_rows, int max_deg, int slots2);
 size_t list_ll_smem_bytes(int E, int n_cols, int Z, int n_tx);
+// kernel: a compiled list kernel (list_jit_kernel), or null for the generic one.
 ldpc_status launch_list_ll(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
-                           int early_stop, cudaStream_t stream);
+                           int early_stop, cudaStream_t stream, const void *kernel = nullptr);
+// Work-list kernels compiled for a set of row sequences (list_jit.cu): the module new
+// work lists use (null: none prepared), its kernel, and the case of a graph's first n_rows
+// rows in it (-1: not among its sequences, the item takes the generic row loop).
+struct ListModule;
+const ListModule *list_jit_active();
+const void *list_jit_kernel(const ListModule *m);
+int list_jit_seq(const ListModule *m, Graph *g, int n_rows);
 ldpc_status launch_list(const ListItem *d_items, int n_items, int *d_counter, size_t smem,
                         int early_stop, cudaStream_t stream);
 

@@ -47,4 +47,16 @@ __host__ __device__ __forceinline__ size_t out_row(const DecodeParams &p, int b)
     return (size_t)(p.out_rows ? p.out_rows[b] : b);
 }
 
+// One codeword of a work list (device side; built by ldpc_decode_list).
+struct ListItem {
+    const uint32_t *edges;    // graph edge table
+    const int *row_ptr;       // graph row pointers
+    const int8_t *llr;        // [n_tx]
+    uint8_t *bits;            // [ceil(K/8)]
+    int32_t *iters;           // [1]
+    int Z, K_b, n_rows, n_cols;
+    int E, n_tx, punct, max_iter;
+    int seq;                  // its row sequence in a compiled list kernel, or -1
+};
+
 }  // namespace ldpc

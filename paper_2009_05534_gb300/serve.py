@@ -165,7 +165,8 @@ class GpuBackend:
     admission from the arena.  ks: information bits per request id.  learned: optional
     LearnedClass; its requests of a slot are decoded by one row-mapped learned decode
     (`ldpc_decode_rows_host_maps`, row maps from host memory) on a stream of its own, into
-    an arena of their own.
+    an arena of their own.  row_tables: optional (base table, n_rows) pairs of the served
+    graphs and rates, for which the work-list kernel is compiled (`ldpc_list_jit_prepare`).
 
     Host work per slot is part of every block's latency (the slot's start event is recorded
     before it), so the per-slot path reuses what does not change: the decode options, the
@@ -174,13 +175,17 @@ class GpuBackend:
 
     def __init__(self, table: np.ndarray, ks: np.ndarray, n_buffers: int, kmax: int,
                  n_streams: int = 4, early_stop: bool = True, keep_results: bool = False,
-                 learned: LearnedClass | None = None):
+                 learned: LearnedClass | None = None, row_tables=None):
         import ctypes
 
         import torch
 
         import paper_2009_05534_gb300 as ldpc
         self.torch, self.ldpc = torch, ldpc
+        if row_tables:
+            # the work-list kernel compiled for the served graphs' row sequences (seconds
+            # of host time, once; the first launch below loads it)
+            ldpc.list_jit_prepare(row_tables)
         self.table = table
         # the table as raw words: row gathers and pointer patches on plain integers
         self.words = np.ascontiguousarray(table, dtype=ldpc.work_item_dtype).view(

@@ -311,3 +311,36 @@ def test_decode_rows_host_maps_equals_gathered_batch(ldpc, dtype):
         ldpc.decode_rows_host_maps(g, pool, np.array([3, -1], np.int32),
                                    np.array([0, 1], np.int32), 8, bits=bits, iters=iters, **kw)
     g.close()
+
+
+@pytest.mark.parametrize("early_stop", [False, True])
+def test_compiled_list_kernel_matches_oracle(ldpc, early_stop):
+    """The work-list kernel compiled for the BG1 row sequences (ldpc_list_jit_prepare): a
+    mixed list whose BG1 items run compiled row sequences and whose BG2 items take the
+    generic row loop in the same launch; every item against the oracle."""
+    tabs = []
+    for rate in RATES["BG1"]:
+        wl = make_workload("BG1", 64, 1, 2.0, rate=Fraction(rate), seed=0, graph_seed=0)
+        tabs.append((wl.base, wl.n_rows))
+    ldpc.list_jit_prepare(tabs)
+    try:
+        graphs, items, refs = _mixed(ldpc, 48, 300 + int(early_stop))
+        assert any(wl.kind == "BG1" for wl, _, _ in refs)
+        assert any(wl.kind == "BG2" for wl, _, _ in refs)
+        for rep in range(2):                         # the first call loads the module
+            for _, _, bits, it, _, _, _ in items:
+                bits.zero_()
+                it.zero_()
+            ldpc.decode_list(items, early_stop=early_stop, threads_per_row=2)
+            torch.cuda.synchronize()
+            for (g, llr, bits, it, n_rows, n_tx, T), (wl, q, _) in zip(items, refs):
+                ref = oracle.decode_layered(wl.base, wl.K_b, wl.Z, wl.n_rows, q,
+                                            algo=oracle.OFFSET, max_iter=T,
+                                            early_stop=early_stop)
+                got = ldpc.unpack_bits(bits.cpu().numpy()[None, :], wl.K)
+                assert np.array_equal(got, ref.bits)
+                assert int(it.item()) == int(ref.iters[0])
+        for g in graphs.values():
+            g.close()
+    finally:
+        ldpc.list_jit_prepare([])

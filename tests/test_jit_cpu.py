@@ -51,3 +51,29 @@ def test_prepare_rejects_bad_sequences(pkg, deg):
     arr = (ctypes.c_int * max(len(deg), 1))(*deg)
     assert pkg.lib().ldpc_pair_jit_prepare(arr, len(deg)) == 1
     assert pkg.lib().ldpc_pair_jit_prepare(None, 3) == 1
+
+
+def test_list_prepare_compiles_a_set_of_sequences(pkg):
+    """The work-list kernel for the BG1- and BG2-shaped tables at two rates each compiles
+    on the host; an empty set switches compiled list kernels off."""
+    from fractions import Fraction
+    from synth import make_workload
+    tabs = []
+    for kind, rates in (("BG1", ("1/3", "8/9")), ("BG2", ("1/3", "5/6"))):
+        for rate in rates:
+            wl = make_workload(kind, 64, 1, 2.0, rate=Fraction(rate), seed=0, graph_seed=0)
+            tabs.append((wl.base, wl.n_rows))
+    pkg.list_jit_prepare(tabs)
+    pkg.list_jit_prepare([])
+
+
+def test_list_prepare_rejects_bad_sets(pkg):
+    import ctypes
+    L = pkg.lib()
+    deg = (ctypes.c_int * 3)(3, 1, 4)
+    rows = (ctypes.c_int * 1)(3)
+    assert L.ldpc_list_jit_prepare(deg, rows, 1) == 1          # a degree below 2
+    assert L.ldpc_list_jit_prepare(None, rows, 1) == 1
+    rows0 = (ctypes.c_int * 1)(0)
+    assert L.ldpc_list_jit_prepare(deg, rows0, 1) == 1         # no rows
+    assert L.ldpc_list_jit_prepare(deg, rows, 65) == 1         # too many sequences
