@@ -27,10 +27,12 @@ def _flags():
             "-Xptxas", "-O3", "--expt-relaxed-constexpr", "-I", BUILD]
 
 
-# Headers the runtime compiler needs for the per-graph batch kernels (pair_jit.cu) and the
-# compiled work-list kernels (list_jit.cu), under the names by which they are included.
+# Headers the runtime compiler needs for the per-graph batch kernels (pair_jit.cu,
+# t16_jit.cu) and the compiled work-list kernels (list_jit.cu), under the names by which
+# they are included.
 JIT_FILES = (("pair_kernel.cuh", os.path.join(CSRC, "pair_kernel.cuh")),
              ("ll_kernel.cuh", os.path.join(CSRC, "ll_kernel.cuh")),
+             ("t16_kernel.cuh", os.path.join(CSRC, "t16_kernel.cuh")),
              ("f16x2.h", os.path.join(CSRC, "f16x2.h")),
              ("ldpc_params.h", os.path.join(CSRC, "ldpc_params.h")),
              ("tmem.h", os.path.join(CSRC, "tmem.h")))

@@ -3,7 +3,10 @@
 
 #include <atomic>
 #include <cstdint>
+#include <functional>
 #include <mutex>
+#include <string>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/ldpc.h"
@@ -87,6 +90,9 @@ ldpc_status launch_rowpair(const DecodeParams &p, int max_deg, cudaStream_t stre
 // (decode_tmem16.cu).
 bool tmem16_supported(const DecodeParams &p, int llr_type, int max_deg, size_t smem_optin);
 ldpc_status launch_tmem16(const DecodeParams &p, cudaStream_t stream);
+// The binary16 kernel compiled at run time for the row sequence of p and a block shape
+// (t16_jit.cu), or null (compilation off, pending or failed: the generic kernel runs).
+const void *t16_jit_kernel(const DecodeParams &p, int cw, bool hybrid);
 
 // Flooding-schedule decoder, fp32 min-sum or sum-product (decode_flooding.cu); ws holds
 // the messages of every codeword.
@@ -115,6 +121,21 @@ ldpc_status launch_list_ll(const ListItem *d_items, int n_items, int *d_counter,
 // Work-list kernels compiled for a set of row sequences (list_jit.cu): the module new
 // work lists use (null: none prepared), its kernel, and the case of a graph's first n_rows
 // rows in it (-1: not among its sequences, the item takes the generic row loop).
+// NVRTC front end (jit_common.cu): the fixed-width type prelude of a runtime-compiled
+// source, and source to cubin for sm_103a (empty on failure; host work only).
+const char *jit_prelude();
+std::vector<char> jit_compile(const std::string &src, const char *name);
+// Registry of runtime-compiled kernels (jit_common.cu), one per key: the kernel `kernel`
+// of the module built from source() (compiled in the background, or waited for in mode 2;
+// null while not ready, when compilation is off or failed); jit_prepare compiles and waits
+// without loading.  Mode 0 off, 1 background (default), 2 blocking; jit_set_mode returns the
+// previous mode plus 4 once a kernel has loaded and 8 once a compilation or load failed.
+int jit_mode();
+int jit_set_mode(int mode);
+const void *jit_kernel(const std::string &key, const std::function<std::string()> &source,
+                       const char *name, const char *kernel);
+bool jit_prepare(const std::string &key, const std::function<std::string()> &source,
+                 const char *name);
 struct ListModule;
 const ListModule *list_jit_active();
 const void *list_jit_kernel(const ListModule *m);

@@ -18,11 +18,8 @@
 #include <string>
 #include <vector>
 
-#include <nvrtc.h>
-
 #include "f16x2.h"
 #include "ldpc_internal.h"
-#include "ldpc_jit_sources.h"
 
 namespace ldpc {
 
@@ -49,19 +46,7 @@ ListRegistry &registry() {
     return *r;
 }
 
-constexpr int kA = 2;                     // cooperating threads per row pair in the list kernel
-
-const char kPrelude[] =
-    "typedef signed char int8_t;\n"
-    "typedef unsigned char uint8_t;\n"
-    "typedef short int16_t;\n"
-    "typedef unsigned short uint16_t;\n"
-    "typedef int int32_t;\n"
-    "typedef unsigned int uint32_t;\n"
-    "typedef long long int64_t;\n"
-    "typedef unsigned long long uint64_t;\n"
-    "typedef unsigned long size_t;\n"
-    "typedef unsigned long uintptr_t;\n";
+constexpr int kA = 2;                     // cooperating threads per row pair (list kernel)
 
 std::string key_of(const int *deg, int n) {
     std::string key;
@@ -90,7 +75,8 @@ std::string case_source(int c, const std::vector<int> &deg) {
     };
     auto row = [&](int r, const std::string &ds, const std::string &de) {
         return " LDPC_LLQ(" + std::to_string(deg[r]) + ", " + std::to_string(s0[r] & 1) +
-               ", (" + std::to_string(s0[r]) + ds + "), (" + std::to_string(e0[r]) + de + "))";
+               ", (" + std::to_string(s0[r]) + ds + "), (" + std::to_string(e0[r]) + de +
+               "))";
     };
     std::string s = " case " + std::to_string(c) + ":";
     int r = 0;
@@ -123,30 +109,11 @@ std::string case_source(int c, const std::vector<int> &deg) {
 }
 
 std::vector<char> compile_list(const std::vector<std::vector<int>> &seqs) {
-    std::string src(kPrelude);
+    std::string src(jit_prelude());
     src += "#define LDPC_LL_SEQS";
     for (size_t c = 0; c < seqs.size(); ++c) src += case_source((int)c, seqs[c]);
     src += "\n#include \"ll_kernel.cuh\"\n";
-    std::vector<const char *> names, texts;
-    for (const auto &f : jitsrc::kFiles) {
-        names.push_back(f.name);
-        texts.push_back(f.text);
-    }
-    std::vector<char> cubin;
-    nvrtcProgram prog;
-    if (nvrtcCreateProgram(&prog, src.c_str(), "ldpc_list_rows.cu", (int)names.size(),
-                           texts.data(), names.data()) != NVRTC_SUCCESS)
-        return cubin;
-    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17"};
-    if (nvrtcCompileProgram(prog, 2, opts) == NVRTC_SUCCESS) {
-        size_t n = 0;
-        if (nvrtcGetCUBINSize(prog, &n) == NVRTC_SUCCESS && n > 0) {
-            cubin.resize(n);
-            if (nvrtcGetCUBIN(prog, cubin.data()) != NVRTC_SUCCESS) cubin.clear();
-        }
-    }
-    nvrtcDestroyProgram(&prog);
-    return cubin;
+    return jit_compile(src, "ldpc_list_rows.cu");
 }
 
 }  // namespace

@@ -103,3 +103,43 @@ def test_background_mode_serves_and_then_switches(ldpc):
             time.sleep(0.25)
     finally:
         ldpc.pair_jit(2)
+
+
+# binary16: the kernel compiled per row sequence and block shape against the generic one
+F16_SHAPES = [("BG1", 384, None, 3, "normalised"), ("BG1", 384, "8/9", 40, "offset"),
+              ("BG2", 128, None, 700, "learned"), ("BG1", 64, None, 20, "normalised")]
+
+
+@pytest.mark.parametrize("kind,Z,rate,B,mode", F16_SHAPES)
+def test_binary16_compiled_equals_generic(ldpc, kind, Z, rate, B, mode):
+    """One, two and four codewords per block (messages all in TMEM, or partly in shared
+    memory for the BG1-shaped Z=384 code at low rate); every output equal, bit for bit."""
+    wl = make_workload(kind, Z, B, 2.5 if rate is None else 7.5,
+                       rate=None if rate is None else Fraction(rate),
+                       modulation="QPSK" if rate is None else "16QAM", seed=B)
+    h = torch.from_numpy(wl.llr_fp16()).cuda()
+    if mode == "normalised":
+        kw = dict(algo=ldpc.NORMALISED, alpha=0.75)
+    elif mode == "offset":
+        kw = dict(algo=ldpc.OFFSET, offset=0.3)
+    else:
+        rng = np.random.default_rng(5)
+        tab = np.zeros((6, wl.n_rows, 2), np.float32)
+        tab[..., 0] = rng.uniform(0.4, 1.0, size=(6, wl.n_rows))
+        tab[..., 1] = rng.uniform(0.0, 0.5, size=(6, wl.n_rows))
+        kw = dict(algo=ldpc.LEARNED, learned=torch.from_numpy(tab).cuda())
+    outs = []
+    for m in (2, 0):
+        prev = ldpc.pair_jit(m) & 3
+        try:
+            g = ldpc.Graph(wl.base, wl.K_b, wl.Z)
+            o = ldpc.decode(g, h, 6, early_stop=True, n_rows=wl.n_rows, n_tx=wl.n_tx,
+                            debug=True, **kw)
+            torch.cuda.synchronize()
+            g.sync_status()
+            g.close()
+            outs.append([x.cpu().numpy() for x in o])
+        finally:
+            ldpc.pair_jit(prev)
+    for a, b in zip(*outs):
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
