@@ -346,9 +346,10 @@ uint64_t ldpc_launch_count(void);
  * diagnostic. */
 uint64_t ldpc_alloc_count(void);
 
-/* The 8-bit batch kernel (threads_per_row 1; the layered schedule of Sec. III) compiled at
- * run time for the degree sequence of the rows a decode uses, so that the layers of an
- * iteration run as straight-line code instead of one indirect branch per row.  Compiling
+/* The 8-bit batch kernel (threads_per_row 1; the layered schedule of Sec. III) and the
+ * binary16 kernel compiled at run time for the degree sequence of the rows a decode uses,
+ * so that the layers of an iteration run as straight-line code instead of one indirect
+ * branch per row.  Compiling
  * (NVRTC) takes a few seconds of host time per new degree sequence; the module is then
  * kept for the process's lifetime.  Results are bit-identical to the generic kernel's,
  * which runs whenever no compiled kernel is ready.
@@ -357,6 +358,9 @@ uint64_t ldpc_alloc_count(void);
  *           the generic kernel until it is ready.
  *   mode 2: the decode that meets a new sequence compiles it and waits (for throughput
  *           runs: compile during warm-up).
+ *   mode 3: no change; wait until no background compilation runs.  A process must not
+ *           exit while one runs (the compiler's exit-time cleanup may run under it): call
+ *           this first (the Python binding does so when the interpreter exits).
  *   any other value: no change.
  * Returns the mode before the call (bits 0-1), plus 4 once a kernel has been compiled and
  * loaded and 8 once a compilation or load has failed since the library was loaded.

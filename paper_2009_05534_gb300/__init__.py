@@ -106,6 +106,9 @@ def lib():
             L.ldpc_alloc_count.restype = ctypes.c_uint64
             L.ldpc_pair_jit.argtypes = [i]
             L.ldpc_pair_jit.restype = i
+            # background compilations must end before the process exits
+            import atexit
+            atexit.register(L.ldpc_pair_jit, 3)
             L.ldpc_pair_jit_prepare.argtypes = [P, i]
             L.ldpc_pair_jit_prepare.restype = i
             L.ldpc_list_jit_prepare.argtypes = [P, P, i]
@@ -143,8 +146,8 @@ def alloc_count() -> int:
 
 
 def pair_jit(mode: int = -1) -> int:
-    """The per-graph compiled batch kernel: 0 off, 1 compile in the background (default),
-    2 compile at first use and wait, -1 only query.  Returns the previous mode (bits 0-1),
+    """The per-graph compiled batch kernels: 0 off, 1 compile in the background (default),
+    2 compile at first use and wait, 3 wait for background compilations, -1 only query.  Returns the previous mode (bits 0-1),
     plus 4 once a kernel has been compiled and 8 once a compilation has failed
     (ldpc_pair_jit)."""
     return int(lib().ldpc_pair_jit(int(mode)))

@@ -86,6 +86,25 @@ JitRegistry &registry() {
     return *r;
 }
 
+// Background compilations in flight.  A process must not exit while one runs: the runtime
+// compiler's own exit-time cleanup can run first and tear its state down under the thread.
+// ldpc_pair_jit(3) waits for them (the Python binding calls it from an interpreter exit
+// hook, which runs before any C exit handler); the destructor waits as well, for the exit
+// orders where it runs first.
+struct JitThreads {
+    std::mutex mu;
+    std::condition_variable cv;
+    int running = 0;
+    ~JitThreads() {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [this] { return running == 0; });
+    }
+};
+JitThreads &threads() {
+    static JitThreads t;
+    return t;
+}
+
 std::atomic<int> g_mode{1};          // 0 off, 1 background compile, 2 blocking compile
 std::atomic<int> g_built{0}, g_failed{0};
 
@@ -133,14 +152,25 @@ JitEntry *entry_for(std::unique_lock<std::mutex> &lk, const std::string &key,
             finish_compile(key, jit_compile(source(), name));
             lk.lock();
         } else {
+            JitThreads &T = threads();
+            {
+                std::lock_guard<std::mutex> tl(T.mu);
+                ++T.running;
+            }
             try {
                 std::string src = source();
                 std::string nm(name);
-                std::thread([key, src, nm] { finish_compile(key, jit_compile(src, nm.c_str())); })
-                    .detach();
+                std::thread([key, src, nm, &T] {
+                    finish_compile(key, jit_compile(src, nm.c_str()));
+                    std::lock_guard<std::mutex> tl(T.mu);
+                    --T.running;
+                    T.cv.notify_all();
+                }).detach();
             } catch (...) {                  // no thread: this key keeps the generic kernel
                 R.entries[key].state = kFailed;
                 g_failed.fetch_add(1);
+                std::lock_guard<std::mutex> tl(T.mu);
+                --T.running;
             }
         }
         it = R.entries.find(key);
@@ -157,6 +187,11 @@ int jit_mode() { return g_mode.load(std::memory_order_relaxed); }
 int jit_set_mode(int mode) {
     const int prev = g_mode.load();
     if (mode >= 0 && mode <= 2) g_mode.store(mode);
+    if (mode == 3) {                         // wait for the background compilations
+        JitThreads &T = threads();
+        std::unique_lock<std::mutex> lk(T.mu);
+        T.cv.wait(lk, [&T] { return T.running == 0; });
+    }
     return prev | (g_built.load() > 0 ? 4 : 0) | (g_failed.load() > 0 ? 8 : 0);
 }
 

@@ -472,11 +472,13 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
     uint8_t *d_bits = (uint8_t *)(base + up(in_b));
     int32_t *d_it = (int32_t *)(base + up(in_b) + up(bits_b));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // Pipeline: the inputs go up in chunks of one wave of codewords (two per SM) on the
-    // graph's copy stream, and the decode of chunk k waits only for chunk k's upload, so
-    // later uploads overlap earlier decodes; each chunk's outputs come back on `stream`
-    // right after its decode.  A wave-sized chunk needs the same number of passes of the
-    // batch kernels as the whole batch would.
+    // Pipeline: the inputs go up in chunks on the graph's copy stream, and the decode of
+    // chunk k waits only for chunk k's upload, so later uploads overlap earlier decodes;
+    // each chunk's outputs come back on `stream` right after its decode.  Chunks grow
+    // geometrically (up to 8 times the previous one): an upload is more than ten times
+    // faster than the decode of the same codewords, so each still hides behind the decode
+    // before it, and the batch kernel, which balances codewords over the SMs by itself,
+    // runs as few launches as that allows (each launch pays its own ramp-up and last round).
     int dev = 0, n_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -486,16 +488,16 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
     int start[Graph::kHostChunks + 1];
     int n_chunks = 0;
     {
-        int chunk = 2 * n_sm;
-        int first = (o.llr_type == LDPC_LLR_INT8 && batch > 2 * n_sm) ? n_sm : chunk;
-        if (1 + (batch - first + chunk - 1) / chunk > Graph::kHostChunks) {
-            chunk = (batch + Graph::kHostChunks - 1) / Graph::kHostChunks;
-            first = chunk;
-        }
+        int chunk = (o.llr_type == LDPC_LLR_INT8 && batch > 2 * n_sm) ? n_sm : 2 * n_sm;
         start[0] = 0;
-        for (int b = first < batch ? first : batch;; b = b + chunk < batch ? b + chunk : batch) {
+        int b = 0;
+        while (b < batch) {
+            // the last chunk takes the rest
+            const int rest = batch - b;
+            const int c = (n_chunks + 1 == Graph::kHostChunks || chunk >= rest) ? rest : chunk;
+            b += c;
             start[++n_chunks] = b;
-            if (b == batch) break;
+            chunk = 8 * c;
         }
     }
     for (int k = 0; k < n_chunks; ++k) {

@@ -143,3 +143,26 @@ def test_binary16_compiled_equals_generic(ldpc, kind, Z, rate, B, mode):
             ldpc.pair_jit(prev)
     for a, b in zip(*outs):
         assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+
+
+def test_exit_during_background_compile_is_clean(ldpc):
+    """A process that meets a new row sequence in the background mode and exits at once
+    (the compilation still running) exits cleanly: the binding waits for it at exit."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys, torch; sys.path.insert(0, %r)\n"
+        "import paper_2009_05534_gb300 as ldpc\n"
+        "from synth import make_workload\n"
+        "ldpc.pair_jit(1)\n"
+        "wl = make_workload('BG2', 96, 4, 2.0, seed=4242)\n"
+        "g = ldpc.Graph(wl.base, wl.K_b, wl.Z)\n"
+        "ldpc.decode(g, torch.from_numpy(wl.llr_int8()).cuda(), 5, threads_per_row=1)\n"
+        "torch.cuda.synchronize()\n"
+        "print('decoded', flush=True)\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "decoded" in r.stdout
