@@ -80,9 +80,10 @@ typedef enum {
  *                per thread block); 2 or 4 = the low-latency strategy (alpha threads split
  *                each row's circulants and combine min, sub-min and sign by a log2(alpha)
  *                step warp-shuffle reduce; one codeword per thread block); int8 only.
- *                0 = automatic: 1 when the batch kernel compiled for the graph's row
- *                sequence is ready (ldpc_pair_jit) or the batch exceeds the SM count,
- *                else 2 when the graph fits.  Results are identical for every value. */
+ *                0 = automatic: 1 when the batch exceeds the SM count; else 2 when the
+ *                graph fits, unless only the batch kernel's compiled form (ldpc_pair_jit)
+ *                is ready for the graph's row sequence and the low-latency kernel's is
+ *                not (then 1).  Results are identical for every value. */
 typedef struct {
     int llr_type;
     int algo;
@@ -346,10 +347,10 @@ uint64_t ldpc_launch_count(void);
  * diagnostic. */
 uint64_t ldpc_alloc_count(void);
 
-/* The 8-bit batch kernel (threads_per_row 1; the layered schedule of Sec. III) and the
- * binary16 kernel compiled at run time for the degree sequence of the rows a decode uses,
- * so that the layers of an iteration run as straight-line code instead of one indirect
- * branch per row.  Compiling
+/* The 8-bit batch kernel (threads_per_row 1; the layered schedule of Sec. III), the
+ * low-latency kernel (threads_per_row 2 and 4) and the binary16 kernel compiled at run time
+ * for the degree sequence of the rows a decode uses, so that the layers of an iteration run
+ * as straight-line code instead of one indirect branch per row.  Compiling
  * (NVRTC) takes a few seconds of host time per new degree sequence; the module is then
  * kept for the process's lifetime.  Results are bit-identical to the generic kernel's,
  * which runs whenever no compiled kernel is ready.

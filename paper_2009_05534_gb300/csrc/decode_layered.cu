@@ -272,14 +272,20 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
         return launch_cluster(p, stream);
     }
     // the low-latency strategy (alpha cooperating threads per row pair, one codeword per
-    // block) when asked for, or by default when the batch does not fill the SMs, unless the
-    // batch kernel compiled for this row sequence is ready: it is the faster one at every
-    // batch size (a lone BG1-shaped Z=384 codeword, 10 iterations: 182 vs 228 us)
+    // block) when asked for, or by default when the batch does not fill the SMs.  Compiled
+    // for the row sequence it is the fastest for such batches (a lone BG1-shaped Z=384
+    // codeword, 10 iterations: 162 us at alpha 2 against 187 us for the compiled batch
+    // kernel); while only the batch kernel's compiled form is ready, that one (230 us for
+    // the generic alpha 2)
     int A = p.threads_per_row;
     if (A == 0) {
-        const bool pair_ok = pair_supported(p, llr_type, p.max_deg, (size_t)smem_optin);
-        A = (p.batch <= n_sm && !(pair_ok && pair_jit_kernel(p)) &&
-             tmem_ll_supported(p, llr_type, p.max_deg, 2, (size_t)smem_optin)) ? 2 : 1;
+        A = 1;
+        if (p.batch <= n_sm &&
+            tmem_ll_supported(p, llr_type, p.max_deg, 2, (size_t)smem_optin)) {
+            const bool pair_ok = pair_supported(p, llr_type, p.max_deg, (size_t)smem_optin);
+            const bool ll_ready = ll_jit_kernel(p, 2) != nullptr;
+            A = (ll_ready || !(pair_ok && pair_jit_kernel(p))) ? 2 : 1;
+        }
     }
     if (A > 1) {
         if (!tmem_ll_supported(p, llr_type, p.max_deg, A, (size_t)smem_optin))

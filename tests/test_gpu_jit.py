@@ -166,3 +166,36 @@ def test_exit_during_background_compile_is_clean(ldpc):
                        timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert "decoded" in r.stdout
+
+
+@pytest.mark.parametrize("tpr", [2, 4])
+@pytest.mark.parametrize("kind,Z,rate,B,ebn0", [("BG1", 384, None, 3, 1.25),
+                                                ("BG2", 96, "1/3", 40, 2.0),
+                                                ("BG1", 40, "1/2", 17, 2.5)])
+def test_low_latency_compiled_equals_oracle_and_generic(ldpc, tpr, kind, Z, rate, B, ebn0):
+    """The one-codeword low-latency kernel (alpha = 2, 4) compiled for the row sequence:
+    every output against the oracle and the generic kernel, with the stopping rule."""
+    wl = make_workload(kind, Z, B, ebn0, rate=None if rate is None else Fraction(rate),
+                       seed=Z + B + tpr)
+    q = wl.llr_int8()
+    outs = []
+    for m in (2, 0):
+        prev = ldpc.pair_jit(m) & 3
+        try:
+            g = ldpc.Graph(wl.base, wl.K_b, wl.Z)
+            o = ldpc.decode(g, torch.from_numpy(q).cuda(), 6, early_stop=True,
+                            n_rows=wl.n_rows, n_tx=wl.n_tx, debug=True, threads_per_row=tpr)
+            torch.cuda.synchronize()
+            g.sync_status()
+            g.close()
+            outs.append([x.cpu().numpy() for x in o])
+        finally:
+            ldpc.pair_jit(prev)
+    ref = _oracle(wl, q, 6, True)
+    got = outs[0]
+    assert np.array_equal(ldpc.unpack_bits(got[0], wl.K), ref.bits)
+    assert np.array_equal(got[1], ref.iters)
+    assert np.array_equal(got[2], ref.post)
+    assert np.array_equal(got[3], ref.c2v)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
