@@ -368,7 +368,8 @@ uint64_t ldpc_alloc_count(void);
  * Process-wide; never fails. */
 int ldpc_pair_jit(int mode);
 
-/* Compile (and wait for) the batch kernel of ldpc_pair_jit for a degree sequence:
+/* Compile (and wait for) the 8-bit kernels of ldpc_pair_jit (the batch kernel and the
+ * low-latency kernel at alpha 2 and 4) for a degree sequence:
  * row_degrees (host, n_rows entries, each 2..20) are the degrees of the rows a decode will
  * use, in order.  Host work only (no CUDA call; the first decode with the sequence loads
  * the module), so a throughput run can compile before its warm-up.  Returns LDPC_OK

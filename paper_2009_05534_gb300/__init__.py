@@ -154,9 +154,9 @@ def pair_jit(mode: int = -1) -> int:
 
 
 def pair_jit_prepare(base, n_rows: int = 0) -> None:
-    """Compile the per-graph batch kernel for the first n_rows rows (0: all) of a base
-    table (int array [M][N], -1 = no circulant) and wait (ldpc_pair_jit_prepare); raises
-    when the sequence is invalid or the compilation failed."""
+    """Compile the 8-bit kernels (batch, and low-latency at alpha 2 and 4) for the first
+    n_rows rows (0: all) of a base table (int array [M][N], -1 = no circulant) and wait
+    (ldpc_pair_jit_prepare); raises when the sequence is invalid or a compilation failed."""
     import numpy as np
     b = np.asarray(base)
     n = int(n_rows) or b.shape[0]

@@ -80,8 +80,10 @@ ldpc_status launch_cluster(const DecodeParams &p, cudaStream_t stream);
 bool tmem_ll_supported(const DecodeParams &p, int llr_type, int max_deg, int A,
                        size_t smem_optin);
 ldpc_status launch_tmem_ll(const DecodeParams &p, int A, cudaStream_t stream);
-// tmem_ll_kernel compiled at run time for the row sequence of p (list_jit.cu), or null.
+// tmem_ll_kernel compiled at run time for the row sequence of p (list_jit.cu), or null;
+// ll_jit_prepare compiles it for a degree sequence and waits (host work only).
 const void *ll_jit_kernel(const DecodeParams &p, int A);
+bool ll_jit_prepare(const std::vector<int> &deg, int A);
 
 // Row-pair fp16x2 kernel for 8-bit offset min-sum, messages in shared memory
 // (decode_rowpair.cu).

@@ -221,24 +221,38 @@ extern "C" ldpc_status ldpc_list_jit_prepare(const int *row_degrees, const int *
 
 namespace ldpc {
 
+namespace {
+
+std::string ll_key(const std::vector<int> &deg, int A) {
+    std::string key = "ll:" + std::to_string(A) + ":";
+    for (const int d : deg) {
+        key += std::to_string(d);
+        key += ',';
+    }
+    return key;
+}
+
+std::string ll_source(const std::vector<int> &deg, int A) {
+    return std::string(jit_prelude()) + "#define LDPC_LL_A " + std::to_string(A) +
+           "\n#define LDPC_LL_ROWS" + ll_rows(deg, A, "LDPC_LLR") +
+           "\n#include \"ll_kernel.cuh\"\n";
+}
+
+}  // namespace
+
 // The one-codeword low-latency kernel compiled for the row sequence of p and A cooperating
 // threads per row pair (registry of jit_common.cu; ldpc_pair_jit's mode applies), or null.
 const void *ll_jit_kernel(const DecodeParams &p, int A) {
     if (jit_mode() == 0) return nullptr;
     std::vector<int> deg((size_t)p.n_rows);
-    std::string key = "ll:" + std::to_string(A) + ":";
-    for (int r = 0; r < p.n_rows; ++r) {
-        deg[(size_t)r] = p.h_row_ptr[r + 1] - p.h_row_ptr[r];
-        key += std::to_string(deg[(size_t)r]);
-        key += ',';
-    }
-    return jit_kernel(key,
-                      [&deg, A] {
-                          return std::string(jit_prelude()) + "#define LDPC_LL_A " +
-                                 std::to_string(A) + "\n#define LDPC_LL_ROWS" +
-                                 ll_rows(deg, A, "LDPC_LLR") + "\n#include \"ll_kernel.cuh\"\n";
-                      },
+    for (int r = 0; r < p.n_rows; ++r) deg[(size_t)r] = p.h_row_ptr[r + 1] - p.h_row_ptr[r];
+    return jit_kernel(ll_key(deg, A), [&deg, A] { return ll_source(deg, A); },
                       "ldpc_ll_rows.cu", "tmem_ll_kernel");
+}
+
+bool ll_jit_prepare(const std::vector<int> &deg, int A) {
+    return jit_prepare(ll_key(deg, A), [&deg, A] { return ll_source(deg, A); },
+                       "ldpc_ll_rows.cu");
 }
 
 }  // namespace ldpc

@@ -107,8 +107,11 @@ extern "C" ldpc_status ldpc_pair_jit_prepare(const int *row_degrees, int n_rows)
         E += row_degrees[r];
     }
     if (E > ldpc::kMaxEdges) return LDPC_ERR_INVALID_ARG;
-    return ldpc::jit_prepare(ldpc::degree_key(deg), [&deg] { return ldpc::module_source(deg); },
-                             "ldpc_pair_rows.cu")
-               ? LDPC_OK
-               : LDPC_ERR_UNSUPPORTED;
+    // the batch kernel and the low-latency kernel at both alphas
+    const bool ok = ldpc::jit_prepare(ldpc::degree_key(deg),
+                                      [&deg] { return ldpc::module_source(deg); },
+                                      "ldpc_pair_rows.cu");
+    const bool ok2 = ldpc::ll_jit_prepare(deg, 2);
+    const bool ok4 = ldpc::ll_jit_prepare(deg, 4);
+    return ok && ok2 && ok4 ? LDPC_OK : LDPC_ERR_UNSUPPORTED;
 }
