@@ -274,9 +274,9 @@ ldpc_status launch_layered(const DecodeParams &p, int llr_type, cudaStream_t str
     // the low-latency strategy (alpha cooperating threads per row pair, one codeword per
     // block) when asked for, or by default when the batch does not fill the SMs.  Compiled
     // for the row sequence it is the fastest for such batches (a lone BG1-shaped Z=384
-    // codeword, 10 iterations: 162 us at alpha 2 against 187 us for the compiled batch
-    // kernel); while only the batch kernel's compiled form is ready, that one (230 us for
-    // the generic alpha 2)
+    // codeword, 10 iterations: 157 us at alpha 2 against 181 us for the compiled batch
+    // kernel); while only the batch kernel's compiled form is ready, that one is used
+    // instead (the generic alpha-2 kernel takes 230 us)
     int A = p.threads_per_row;
     if (A == 0) {
         A = 1;
