@@ -1,7 +1,8 @@
-// NVRTC front end shared by the runtime-compiled kernels of list_jit.cu and t16_jit.cu:
-// one source (the fixed-width type prelude, the caller's macros, the kernel header) to a
-// cubin for sm_103a, with the kernel headers embedded at build time (ldpc_jit_sources.h).
-// Host work only; no CUDA call.
+// NVRTC front end shared by the runtime-compiled kernels of pair_jit.cu, list_jit.cu and
+// t16_jit.cu: one source (the fixed-width type prelude, the caller's macros, the kernel
+// header) to a cubin for sm_103a, with the kernel headers embedded at build time
+// (ldpc_jit_sources.h); and the registry of compiled kernels, which loads their modules on
+// the launching thread.
 #include <string>
 #include <vector>
 
