@@ -10,7 +10,9 @@ the hot path: load, gather, v->c, check node, write-back, output).
 
 Metric: decoded information Gbit/s = batch * K / time, timed with CUDA events on the
 decode stream; inputs rotate over device copies totalling more than twice the L2 size, so
-no step reads its LLRs from L2.  `--impl reference` times the CPU oracle instead.
+no step reads its LLRs from L2.  `--impl reference` times the CPU oracle instead.  The
+clock record (nvidia-smi every 200 ms) spans the timed region and 1.5 s of the same decode
+run untimed right after it, since the timed region is shorter than one sampling period.
 
 Beside the headline the JSON line carries: the ALU roofline fraction and the profiled DRAM
 traffic of the decode kernel; the early-stop figure; an end-to-end figure through the
