@@ -186,12 +186,14 @@ ldpc_status ldpc_decode_debug(ldpc_graph_t g, const void *llr_dev, int batch, in
  *                   copies; pageable memory works).
  *   hard_bits_host  host uint8 [batch][ceil(K/8)];  iters_host  host int32 [batch].
  * The graph keeps device staging buffers (grown on demand, reused across calls) and a copy
- * stream; the call copies the LLRs in on that stream in chunks of one wave of codewords
- * (two per SM), decodes each chunk on `stream` as soon as its copy has landed (so later
- * copies overlap earlier decodes), copies each chunk's results out on `stream`, and
- * returns after all results are in host memory.  Results equal those of ldpc_decode on
- * the same LLRs.  Calls on the same graph from several threads are serialised.
- * LDPC_ERR_OUT_OF_MEMORY if the staging buffers cannot be allocated. */
+ * stream; the call copies the LLRs in on that stream in chunks (the first one codeword per
+ * SM for int8 batches above two per SM, else two per SM; each next one up to 8 times the
+ * previous, at most a few chunks), decodes each chunk on `stream` as soon as its copy has
+ * landed (so later copies overlap earlier decodes), copies each chunk's results out on
+ * `stream`, and returns after all results are in host memory.  Results equal those of
+ * ldpc_decode on the same LLRs.  Calls on the same graph from several threads are
+ * serialised.  Argument errors are those of ldpc_decode, found before anything is
+ * allocated or copied; LDPC_ERR_OUT_OF_MEMORY if the staging buffers cannot be allocated. */
 ldpc_status ldpc_decode_host(ldpc_graph_t g, const void *llr_host, int batch, int max_iter,
                              ldpc_stream_t stream, const ldpc_decode_opts *opts,
                              uint8_t *hard_bits_host, int32_t *iters_host);

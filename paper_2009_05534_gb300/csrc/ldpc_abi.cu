@@ -276,7 +276,8 @@ static ldpc_status decode_params(ldpc_graph_t h, const void *llr, int batch, int
     if (g->min_deg_upto[n_rows] < 2) return LDPC_ERR_UNSUPPORTED;
     if (o.punct_cols < 0 || o.punct_cols > n_cols) return LDPC_ERR_INVALID_ARG;
     const int n_tx = o.n_tx == 0 ? (n_cols - o.punct_cols) * g->Z : o.n_tx;
-    if (n_tx < 0 || o.punct_cols * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+    // (written without a sum that a huge n_tx could overflow)
+    if (n_tx < 0 || n_tx > (n_cols - o.punct_cols) * g->Z) return LDPC_ERR_INVALID_ARG;
     if (batch == 0) {
         *empty = true;
         return LDPC_OK;
@@ -434,9 +435,17 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
         o = *opts;
     else
         ldpc_decode_opts_default(&o);
-    if (batch < 0) return LDPC_ERR_INVALID_ARG;
-    if (batch == 0) return LDPC_OK;
-    if (!llr_host || !hard_bits_host || !iters_host) return LDPC_ERR_INVALID_ARG;
+    // every argument is checked before anything is allocated or copied (the decode's own
+    // checks; the pointers here are host pointers, which it only tests for null)
+    {
+        ldpc::DecodeParams pv;
+        ldpc_decode_opts ov;
+        bool empty = false;
+        const ldpc_status st = decode_params(h, llr_host, batch, max_iter, &o, hard_bits_host,
+                                             iters_host, nullptr, nullptr, false, &pv, &ov,
+                                             &empty);
+        if (st != LDPC_OK || empty) return st;
+    }
     const int n_rows = o.n_rows == 0 ? g->M_bg : o.n_rows;
     if (n_rows < 1 || n_rows > g->M_bg || o.punct_cols < 0) return LDPC_ERR_INVALID_ARG;
     const int n_cols = g->K_b + n_rows;
@@ -497,7 +506,7 @@ ldpc_status ldpc_decode_host(ldpc_graph_t h, const void *llr_host, int batch, in
             const int c = (n_chunks + 1 == Graph::kHostChunks || chunk >= rest) ? rest : chunk;
             b += c;
             start[++n_chunks] = b;
-            chunk = 8 * c;
+            chunk = c > batch / 8 ? batch : 8 * c;
         }
     }
     for (int k = 0; k < n_chunks; ++k) {
@@ -565,7 +574,7 @@ ldpc_status ldpc_decode_list(const ldpc_work_item *items, int n_items, ldpc_stre
         const int n_cols = g->K_b + n_rows;
         if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
         const int n_tx = w.n_tx == 0 ? (n_cols - 2) * g->Z : w.n_tx;
-        if (n_tx < 0 || 2 * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+        if (n_tx < 0 || n_tx > (n_cols - 2) * g->Z) return LDPC_ERR_INVALID_ARG;
         const int E = g->row_ptr[n_rows];
         if (g->min_deg_upto[n_rows] < 2 ||
             !ldpc::list_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows]))
@@ -673,7 +682,7 @@ static ldpc_status prepare_list_noalloc(const ldpc_work_item *items, int n_items
         const int n_cols = g->K_b + n_rows;
         if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
         const int n_tx = w.n_tx == 0 ? (n_cols - 2) * g->Z : w.n_tx;
-        if (n_tx < 0 || 2 * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+        if (n_tx < 0 || n_tx > (n_cols - 2) * g->Z) return LDPC_ERR_INVALID_ARG;
         const int E = g->row_ptr[n_rows];
         if (g->min_deg_upto[n_rows] < 2 ||
             !ldpc::list_item_supported(g->Z, E, n_rows, g->max_deg_upto[n_rows]))
@@ -745,7 +754,7 @@ static ldpc_status learned_common(ldpc_graph_t h, int batch, int T, int n_rows_i
     if (n_cols > g->N_bg || g->max_col_upto[n_rows] >= n_cols) return LDPC_ERR_INVALID_ARG;
     if (g->min_deg_upto[n_rows] < 2) return LDPC_ERR_UNSUPPORTED;
     const int n_tx = n_tx_in == 0 ? (n_cols - 2) * g->Z : n_tx_in;
-    if (n_tx < 0 || 2 * g->Z + n_tx > n_cols * g->Z) return LDPC_ERR_INVALID_ARG;
+    if (n_tx < 0 || n_tx > (n_cols - 2) * g->Z) return LDPC_ERR_INVALID_ARG;
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != g->device) return LDPC_ERR_INVALID_ARG;

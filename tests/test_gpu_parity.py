@@ -166,6 +166,8 @@ def test_invalid_calls_raise(ldpc):
         ldpc.decode(g, q, 5, algo=ldpc.NORMALISED)   # int8 supports offset only
     with pytest.raises(ldpc.LdpcError):
         ldpc.decode(g, q, 5, n_tx=10 ** 6)
+    with pytest.raises(ldpc.LdpcError):              # no 32-bit sum with n_tx may wrap
+        ldpc.decode(g, q, 5, n_tx=2 ** 31 - 1)
     with pytest.raises(ldpc.LdpcError):
         ldpc.decode(g, q, 5, threads_per_row=3)      # alpha must be 0, 1, 2 or 4
     with pytest.raises(ldpc.LdpcError):                # low latency: int8 offset only
